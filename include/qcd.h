@@ -1,0 +1,208 @@
+/*
+ * libqcd: GB300 (sm_103a) even-odd Wilson / twisted-mass Wilson operator and
+ * CG solver, C ABI.
+ *
+ * The paper (CL2QCD, arXiv:1411.5219) names the most expensive part of a
+ * lattice QCD simulation as the inversion of the fermion matrix, D phi = psi,
+ * by a Krylov method such as CG, in which the product D phi -- dominated by
+ * its hopping part, the "Dslash" -- is applied many times and is limited by
+ * memory bandwidth (Sec. 1).  It implements Wilson and twisted-mass Wilson
+ * fermions (Sec. 3), on structure-of-arrays device buffers (Sec. 4), in
+ * double precision (Sec. 4).  This library provides that hot path:
+ *
+ *   D_hop psi(x) = sum_mu [ (1 - gamma_mu) U_mu(x) psi(x+mu)
+ *                         + (1 + gamma_mu) U_mu(x-mu)^dagger psi(x-mu) ]
+ *   M = A - kappa D_hop,   A = 1 + i a gamma_5,   a = 2 kappa mu
+ *
+ * with gamma matrices in the chiral basis (gamma_k = [[0, -i sigma_k],
+ * [i sigma_k, 0]], gamma_4 = [[0, 1], [1, 0]], gamma_5 = diag(1,1,-1,-1)),
+ * periodic boundaries in space and the factor t_bc on hops that wrap in
+ * time.  The paper gives no formulas; these conventions are the standard
+ * ones.  Even-odd preconditioning and mixed precision are not in the paper;
+ * they are the usual way to run this inversion fast:
+ *
+ *   Mhat = A - kappa^2 D_eo A^-1 D_oe   on even sites (Schur complement),
+ *   A^-1 = (1 - i a gamma_5) / (1 + a^2).
+ *
+ * Sites: lex = x + Lx*(y + Ly*(z + Lz*t)); parity p = (x+y+z+t) mod 2.  A
+ * half field holds the sites of one parity; its host form is
+ * parity-compacted, site lex at index lex/2.
+ *
+ * Host layouts (interleaved re/im doubles, C order):
+ *   gauge   [t][z][y][x][mu][a][b]   (mu = 0..3 for x, y, z, t; U_mu(x)[a][b])
+ *   spinor  [t][z][y][x][spin][colour]        full field, 24 doubles per site
+ *   half    [lex/2][spin][colour]             one parity, 24 doubles per site
+ *
+ * Conventions of every call:
+ *   - Returns a qcd_status; no C++ exception crosses the ABI.
+ *     qcd_last_error() gives a message for the last failure on this thread.
+ *   - `stream` is a cudaStream_t (NULL: the legacy default stream).  Calls
+ *     are asynchronous on it unless stated otherwise; host buffers passed to
+ *     upload/download must stay valid until the stream reaches the copy
+ *     (the call returns only after the copy when the buffer is pageable).
+ *   - The library owns every handle and the device memory it allocates;
+ *     destroy each handle once; destroying NULL is a no-op.  A handle must
+ *     outlive the work queued on it.
+ *   - Work on handles of the same lattice must be ordered on one stream:
+ *     a lattice handle owns the scratch (reductions, staging, solver
+ *     fields) that these calls share.
+ */
+#ifndef QCD_H
+#define QCD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int qcd_status;
+#define QCD_OK 0
+#define QCD_ERR_INVALID_ARG 1   /* bad handle, size, layout or parameter */
+#define QCD_ERR_OOM 2           /* device allocation failed */
+#define QCD_ERR_CUDA 3          /* a CUDA call failed */
+#define QCD_ERR_NOT_CONVERGED 4 /* maxiter reached; x and stats still written */
+#define QCD_ERR_BREAKDOWN 5     /* CG breakdown: <p,Ap> <= 0 or non-finite values */
+#define QCD_ERR_TIMEOUT 6       /* reserved for bounded device waits */
+
+typedef enum { QCD_PREC_F64 = 0, QCD_PREC_F32 = 1, QCD_PREC_F16 = 2, QCD_PREC_BF16 = 3 } qcd_prec;
+/* Link storage: 18 reals (full matrix) or 12 (rows 0 and 1; row 2 is
+ * rebuilt as conj(row0 x row1), exact for SU(3)). */
+typedef enum { QCD_RECON_18 = 18, QCD_RECON_12 = 12 } qcd_recon;
+typedef enum { QCD_PARITY_EVEN = 0, QCD_PARITY_ODD = 1, QCD_PARITY_FULL = 2 } qcd_parity;
+
+typedef struct qcd_lattice qcd_lattice;
+typedef struct qcd_gauge qcd_gauge;
+typedef struct qcd_spinor qcd_spinor;
+
+/* Name of a status code (static string). */
+const char *qcd_status_string(qcd_status s);
+/* Message of the last failing call on this thread (static, thread-local). */
+const char *qcd_last_error(void);
+/* Library version string. */
+const char *qcd_version(void);
+/* Block the calling thread until all work queued on `stream` is done.
+ * Errors: CUDA (a failure of earlier asynchronous work is reported here). */
+qcd_status qcd_stream_sync(void *stream);
+
+/* ---------------------------------------------------------------- lattice */
+
+/* A lattice Lx x Ly x Lz x Lt on the current CUDA device.  dims[mu] must
+ * be even and >= 2 (even-odd indexing needs even Lx; the boundary factor
+ * needs even extents for a consistent parity).  t_bc = +1 (periodic) or -1
+ * (antiperiodic) in time (Sec. 1 discretises space-time on an Ns^3 x Nt
+ * hypercube).  Errors: INVALID_ARG for bad extents or a volume too large
+ * for 32-bit site indices; OOM. */
+qcd_status qcd_lattice_create(const int dims[4], int t_bc, qcd_lattice **out);
+void qcd_lattice_destroy(qcd_lattice *lat);
+
+/* ------------------------------------------------------------------ gauge */
+
+/* A gauge field U_mu(x) in SU(3) (4 links per site, Sec. 1 and 4), stored
+ * on the device per (parity, mu) block, site-fastest (SoA, Sec. 4), in
+ * precision `prec` and with `recon` reals per link.  The field also keeps
+ * derived copies in other precisions, made on the device from this one on
+ * first use by a Dslash of that precision.  Errors: INVALID_ARG; OOM. */
+qcd_status qcd_gauge_create(const qcd_lattice *lat, qcd_prec prec, qcd_recon recon, qcd_gauge **out);
+/* Copy a host gauge field (host layout above, 4*V*9 complex doubles) to
+ * the device and convert it; drops derived copies.  Recon-12 assumes
+ * SU(3) links.  Errors: INVALID_ARG (NULL); CUDA. */
+qcd_status qcd_gauge_upload(qcd_gauge *g, const double *host, void *stream);
+/* Build (if missing) the derived copy used by kernels of precision
+ * `prec` with `recon` reals per link.  Optional: kernels build it on first
+ * use.  Errors: INVALID_ARG; OOM. */
+qcd_status qcd_gauge_prepare(qcd_gauge *g, qcd_prec prec, qcd_recon recon, void *stream);
+void qcd_gauge_destroy(qcd_gauge *g);
+
+/* ----------------------------------------------------------------- spinor */
+
+/* A spinor (fermion) field, 4 spins x 3 colours per site (Sec. 4), on one
+ * parity (EVEN/ODD, V/2 sites) or on all sites (FULL = even half then odd
+ * half).  F16 keeps one FP32 scale per site.  Errors: INVALID_ARG; OOM. */
+qcd_status qcd_spinor_create(const qcd_lattice *lat, qcd_parity parity, qcd_prec prec, qcd_spinor **out);
+/* Device bytes of such a field: *data_bytes for the planes, *norm_bytes
+ * for the F16 per-site scales (0 otherwise). */
+qcd_status qcd_spinor_bytes(const qcd_lattice *lat, qcd_parity parity, qcd_prec prec, size_t *data_bytes,
+                            size_t *norm_bytes);
+/* A spinor handle over caller-owned device memory of at least the sizes
+ * qcd_spinor_bytes reports (256-byte aligned); the library never frees
+ * it.  `norm` is required for F16 only. */
+qcd_status qcd_spinor_wrap_device(const qcd_lattice *lat, qcd_parity parity, qcd_prec prec, void *data, void *norm,
+                                  qcd_spinor **out);
+/* Host (FP64, host layout above; FULL: V*12 complex, EVEN/ODD: V/2*12
+ * complex) to device, converting to the field's precision. */
+qcd_status qcd_spinor_upload(qcd_spinor *s, const double *host, void *stream);
+/* Device to host (FP64, same layouts).  Asynchronous: synchronise the
+ * stream before reading `host`. */
+qcd_status qcd_spinor_download(const qcd_spinor *s, double *host, void *stream);
+/* Set to zero. */
+qcd_status qcd_spinor_zero(qcd_spinor *s, void *stream);
+/* Copy with precision conversion between fields of the same lattice and
+ * parity. */
+qcd_status qcd_spinor_convert(qcd_spinor *dst, const qcd_spinor *src, void *stream);
+/* result[0] = sum |s|^2 over the field's sites, FP64 accumulation, fixed
+ * summation order.  `result` is a device pointer to 1 double; the value is
+ * ready when the stream reaches it.  Uses the lattice's reduction scratch. */
+qcd_status qcd_spinor_norm2(const qcd_spinor *s, double *result_device, void *stream);
+void qcd_spinor_destroy(qcd_spinor *s);
+
+/* -------------------------------------------------------------- operators */
+
+/* out = D_hop in (dagger = 0) or D_hop^dagger in (dagger = 1): the Dslash
+ * (Sec. 1 and 6).  With out of parity p (EVEN or ODD) and in of parity 1-p
+ * this is the block D_eo (p = EVEN) or D_oe (p = ODD); with both FULL it is
+ * the hopping term on the whole lattice.  out and in share the precision
+ * (F64: FP64 arithmetic; F32/F16/BF16: FP32 arithmetic); the gauge field's
+ * copy in that precision and with the gauge field's recon is used.
+ * Errors: INVALID_ARG (parities, lattices, precisions); CUDA. */
+qcd_status qcd_apply_dslash(const qcd_gauge *g, qcd_spinor *out, const qcd_spinor *in, int dagger, void *stream);
+
+/* eo = 0: out = M in on FULL fields, M = A - kappa D_hop (Wilson, Sec. 3;
+ *         twisted mass for mu != 0, Sec. 3).
+ * eo = 1: out = Mhat in on EVEN fields (Schur complement above).
+ * dagger = 1 applies the adjoint (M^dagger = A^dagger - kappa D_hop^dagger).
+ * F64 fields only.  Errors: INVALID_ARG; CUDA. */
+qcd_status qcd_apply_M(const qcd_gauge *g, qcd_spinor *out, const qcd_spinor *in, double kappa, double mu, int eo,
+                       int dagger, void *stream);
+
+/* ----------------------------------------------------------------- solver */
+
+typedef struct {
+    double kappa;          /* hopping parameter */
+    double mu;             /* twisted mass (0: Wilson) */
+    double tol;            /* target relative residual (e.g. 1e-10) */
+    int maxiter;           /* CG iteration cap */
+    int eo;                /* 1: even-odd Schur complement (solves M x = b) */
+    int normal;            /* eo = 0 only: 1 solves M^dagger M x = b, 0 solves M x = b (CGNR) */
+    qcd_prec inner_prec;   /* F64: plain FP64 CG; F32/F16/BF16: mixed precision with FP64 reliable updates */
+    qcd_recon inner_recon; /* link storage of the inner (sloppy) operator */
+    double reliable_delta; /* mixed: reliable update when |r| < delta * max|r| since the last one (e.g. 0.1) */
+} qcd_solver_params;
+
+typedef struct {
+    int iterations;            /* CG iterations */
+    int reliable_updates;      /* FP64 true-residual recomputations */
+    double true_rel_residual;  /* |rhs - A x| / |rhs| of the CG system, FP64 */
+    double full_rel_residual;  /* |b - M x| / |b| (normal: |b - M^dag M x| / |b|), FP64 */
+    double seconds;            /* wall time of the call */
+} qcd_solver_stats;
+
+/* Solve for x (FULL, F64) given b (FULL, F64) by conjugate gradient (Sec. 1):
+ *   eo = 1:  b'_e = b_e + kappa D_eo A^-1 b_o;  CG on Mhat^dag Mhat x_e =
+ *            Mhat^dag b'_e;  x_o = A^-1 (b_o + kappa D_oe x_e).
+ *   eo = 0:  CG on M^dag M x = b (normal = 1) or = M^dag b (normal = 0).
+ * Stops when the iterated residual reaches tol relative to the CG right-hand
+ * side and the FP64 true residual confirms it (otherwise it restarts the
+ * residual and continues).  Mixed precision runs the inner iterations on
+ * fields and links of `inner_prec` (FP32 arithmetic), accumulates x in FP64
+ * and replaces the residual by the FP64 true residual at each reliable
+ * update.  Blocks until the solve is done.  Returns OK, NOT_CONVERGED
+ * (maxiter; x and stats written), BREAKDOWN, INVALID_ARG, OOM or CUDA. */
+qcd_status qcd_solve_cg(const qcd_gauge *g, qcd_spinor *x, const qcd_spinor *b, const qcd_solver_params *params,
+                        qcd_solver_stats *stats, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QCD_H */

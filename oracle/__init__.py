@@ -51,6 +51,7 @@ def _load():
         lib.oracle_dhop.argtypes = [p, d, p, p, p, i]
         lib.oracle_apply_m.argtypes = [p, d, p, d, d, p, p, i]
         lib.oracle_dhop_eo.argtypes = [p, d, p, i, p, p, i]
+        lib.oracle_dhop_sites.argtypes = [p, d, p, p, p, ctypes.c_long, p, i]
         lib.oracle_apply_mhat.argtypes = [p, d, p, d, d, p, p, i]
         lib.oracle_twist.argtypes = [p, p, ctypes.c_long, d, i]
         for f in (lib.oracle_solve_mdagm, lib.oracle_solve_m, lib.oracle_solve_eo):
@@ -103,6 +104,17 @@ def apply_m(U, psi, kappa, mu=0.0, t_bc=-1.0, dagger=False):
     out = np.empty_like(psi)
     _load().oracle_apply_m(_dims(U), float(t_bc), pu, float(kappa), float(mu), pp,
                            out.ctypes.data_as(ctypes.c_void_p), int(dagger))
+    return out
+
+
+def dhop_sites(U, psi, sites, t_bc=-1.0, dagger=False):
+    """D_hop psi (or D_hop^dagger psi) at the given lexicographic sites only."""
+    U, pu = _c(U)
+    psi, pp = _c(psi)
+    sites = np.ascontiguousarray(sites, dtype=np.int64)
+    out = np.empty((len(sites), 4, 3), dtype=np.complex128)
+    _load().oracle_dhop_sites(_dims(U), float(t_bc), pu, pp, sites.ctypes.data_as(ctypes.c_void_p), len(sites),
+                              out.ctypes.data_as(ctypes.c_void_p), int(dagger))
     return out
 
 

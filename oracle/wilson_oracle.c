@@ -173,49 +173,53 @@ static const su3 *link(const cplx *U, long lex, int mu)
     return (const su3 *)(U + (lex * 4 + mu) * 9);
 }
 
-/* out = D_hop psi (dagger = 0) or D_hop^dagger psi (dagger = 1) at every
- * site.  The adjoint swaps the spin projectors: (1 + gamma_mu) forward,
- * (1 - gamma_mu) backward. */
+/* res = (D_hop psi)(x) (dagger = 0) or (D_hop^dagger psi)(x) (dagger = 1)
+ * at the single site x.  The adjoint swaps the spin projectors: (1 +
+ * gamma_mu) forward, (1 - gamma_mu) backward. */
+static void dhop_site(const lattice *g, const cplx *U, const spinor *psi, long x, int dagger, spinor res)
+{
+    const double sg = dagger ? -1.0 : 1.0;
+    spinor acc;
+    memset(acc, 0, sizeof(acc));
+    for (int mu = 0; mu < 4; ++mu) {
+        for (int dir = +1; dir >= -1; dir -= 2) {
+            double bsign;
+            long y = neighbour(g, x, mu, dir, &bsign);
+            /* colour part: U_mu(x) psi(x+mu)  or  U_mu(x-mu)^dagger psi(x-mu) */
+            spinor chi;
+            const su3 *u = dir > 0 ? link(U, x, mu) : link(U, y, mu);
+            for (int s = 0; s < 4; ++s)
+                for (int a = 0; a < 3; ++a) {
+                    cplx v = 0;
+                    for (int b = 0; b < 3; ++b) {
+                        if (dir > 0)
+                            v += (*u)[a][b] * psi[y][s][b];
+                        else
+                            v += conj((*u)[b][a]) * psi[y][s][b];
+                    }
+                    chi[s][a] = v;
+                }
+            /* spin part: (1 - dir*sg*gamma_mu) chi */
+            const double gs = -dir * sg;
+            for (int s = 0; s < 4; ++s)
+                for (int a = 0; a < 3; ++a) {
+                    cplx gchi = 0;
+                    for (int t = 0; t < 4; ++t) gchi += GAMMA[mu][s][t] * chi[t][a];
+                    acc[s][a] += bsign * (chi[s][a] + gs * gchi);
+                }
+        }
+    }
+    memcpy(res, acc, sizeof(acc));
+}
+
+/* out = D_hop psi (or D_hop^dagger psi) at every site. */
 static void dhop(const lattice *g, const cplx *U, const cplx *in, cplx *out, int dagger)
 {
     init_gamma();
-    const double sg = dagger ? -1.0 : 1.0;
     const spinor *psi = (const spinor *)in;
     spinor *res = (spinor *)out;
 #pragma omp parallel for schedule(static)
-    for (long x = 0; x < g->V; ++x) {
-        spinor acc;
-        memset(acc, 0, sizeof(acc));
-        for (int mu = 0; mu < 4; ++mu) {
-            for (int dir = +1; dir >= -1; dir -= 2) {
-                double bsign;
-                long y = neighbour(g, x, mu, dir, &bsign);
-                /* colour part: U_mu(x) psi(x+mu)  or  U_mu(x-mu)^dagger psi(x-mu) */
-                spinor chi;
-                const su3 *u = dir > 0 ? link(U, x, mu) : link(U, y, mu);
-                for (int s = 0; s < 4; ++s)
-                    for (int a = 0; a < 3; ++a) {
-                        cplx v = 0;
-                        for (int b = 0; b < 3; ++b) {
-                            if (dir > 0)
-                                v += (*u)[a][b] * psi[y][s][b];
-                            else
-                                v += conj((*u)[b][a]) * psi[y][s][b];
-                        }
-                        chi[s][a] = v;
-                    }
-                /* spin part: (1 - dir*sg*gamma_mu) chi */
-                const double gs = -dir * sg;
-                for (int s = 0; s < 4; ++s)
-                    for (int a = 0; a < 3; ++a) {
-                        cplx gchi = 0;
-                        for (int t = 0; t < 4; ++t) gchi += GAMMA[mu][s][t] * chi[t][a];
-                        acc[s][a] += bsign * (chi[s][a] + gs * gchi);
-                    }
-            }
-        }
-        memcpy(res[x], acc, sizeof(acc));
-    }
+    for (long x = 0; x < g->V; ++x) dhop_site(g, U, psi, x, dagger, res[x]);
 }
 
 /* out = (1 + i b gamma_5) in, or its inverse (1 - i b gamma_5)/(1 + b^2)
@@ -427,6 +431,18 @@ void oracle_apply_mhat(const int *dims, double t_bc, const double *U, double kap
 {
     lattice g = make_lattice(dims, t_bc);
     apply_mhat(&g, (const cplx *)U, kappa, mu, (const cplx *)in, (cplx *)out, dagger);
+}
+
+/* D_hop psi (or its adjoint) at the n lexicographic sites listed in
+ * `sites`, from a full input field; out holds n spinors. */
+void oracle_dhop_sites(const int *dims, double t_bc, const double *U, const double *in, const long *sites,
+                       long n, double *out, int dagger)
+{
+    lattice g = make_lattice(dims, t_bc);
+    init_gamma();
+    spinor *res = (spinor *)out;
+#pragma omp parallel for schedule(static)
+    for (long k = 0; k < n; ++k) dhop_site(&g, (const cplx *)U, (const spinor *)in, sites[k], dagger, res[k]);
 }
 
 /* (1 + i b gamma_5) or its inverse on n sites of 12 complex components. */

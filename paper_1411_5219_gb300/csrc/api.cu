@@ -1,0 +1,605 @@
+// C ABI of libqcd: handles, host<->device transfer, operator application.
+// Declarations and argument conventions are in include/qcd.h.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "qcd_handles.h"
+
+namespace qcd {
+
+static thread_local char g_err[512] = "";
+
+qcd_status fail(qcd_status code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+qcd_status check_cuda(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return QCD_OK;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(QCD_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    }
+    if (e == cudaErrorInvalidValue) return fail(QCD_ERR_INVALID_ARG, "%s: unsupported format or argument", what);
+    return fail(QCD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// ----------------------------------------------------------------- sizes
+
+int spinor_planes(int prec) { return prec == QCD_PREC_F64 ? 12 : prec == QCD_PREC_F32 ? 6 : 3; }
+size_t spinor_plane_elem_bytes(int) { return 16; }
+size_t spinor_half_bytes(int prec, int stride) { return (size_t)spinor_planes(prec) * 16 * stride; }
+size_t spinor_half_norm_bytes(int prec, int stride) { return prec == QCD_PREC_F16 ? (size_t)4 * stride : 0; }
+
+int gauge_planes(int prec, int recon)
+{
+    if (prec == QCD_PREC_F64) return recon / 2;
+    return recon == 18 ? 9 : 3;
+}
+size_t gauge_plane_elem_bytes(int prec, int recon)
+{
+    if (prec == QCD_PREC_F64) return 16;
+    if (prec == QCD_PREC_F32) return recon == 18 ? 8 : 16;
+    return recon == 18 ? 4 : 8;
+}
+size_t gauge_bytes(int prec, int recon, int stride)
+{
+    return (size_t)8 * gauge_planes(prec, recon) * gauge_plane_elem_bytes(prec, recon) * stride;
+}
+
+static bool valid_prec(int p) { return p >= QCD_PREC_F64 && p <= QCD_PREC_BF16; }
+static bool valid_recon(int r) { return r == 18 || r == 12; }
+
+// ----------------------------------------------------------------- views
+
+void *workspace(const qcd_lattice *lat, const std::string &name, size_t bytes)
+{
+    auto it = lat->ws.find(name);
+    if (it != lat->ws.end() && it->second.second >= bytes) return it->second.first;
+    if (it != lat->ws.end()) {
+        cudaFree(it->second.first);
+        lat->ws.erase(it);
+    }
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    lat->ws[name] = {p, bytes};
+    return p;
+}
+
+FieldView view_half(const qcd_spinor *s, int half)
+{
+    FieldView f;
+    f.nh = 1;
+    f.h = s->lat->h;
+    f.prec = s->prec;
+    f.hv[0].data = static_cast<char *>(s->data) + half * s->half_data_bytes;
+    f.hv[0].norm = s->norm ? reinterpret_cast<float *>(reinterpret_cast<char *>(s->norm) + half * s->half_norm_bytes)
+                           : nullptr;
+    f.hv[0].stride = s->lat->stride;
+    f.hv[1] = f.hv[0];
+    return f;
+}
+
+FieldView view_of(const qcd_spinor *s)
+{
+    FieldView f = view_half(s, 0);
+    if (s->parity == QCD_PARITY_FULL) {
+        f.nh = 2;
+        f.hv[1] = view_half(s, 1).hv[0];
+    }
+    return f;
+}
+
+FieldView ws_field(const qcd_lattice *lat, const std::string &name, int nh, int prec)
+{
+    const size_t db = spinor_half_bytes(prec, lat->stride), nb = spinor_half_norm_bytes(prec, lat->stride);
+    char *base = static_cast<char *>(workspace(lat, name + "/p" + std::to_string(prec), nh * (db + nb)));
+    FieldView f;
+    f.nh = nh;
+    f.h = lat->h;
+    f.prec = prec;
+    for (int k = 0; k < 2; ++k) {
+        const int kk = k < nh ? k : 0;
+        f.hv[k].data = base ? base + kk * db : nullptr;
+        f.hv[k].norm = (base && nb) ? reinterpret_cast<float *>(base + nh * db + kk * nb) : nullptr;
+        f.hv[k].stride = lat->stride;
+    }
+    return f;
+}
+
+Reduction reduction_of(const qcd_lattice *lat) { return Reduction{lat->red_partials, lat->red_counter}; }
+
+GaugeView gauge_view(const qcd_gauge *g, int prec, int recon, cudaStream_t s, qcd_status *st)
+{
+    *st = QCD_OK;
+    const int stride = g->lat->stride;
+    if (prec == g->prec && recon == g->recon) return GaugeView{g->data, stride};
+    const int key = prec * 100 + recon;
+    auto *gm = const_cast<qcd_gauge *>(g);
+    auto it = gm->derived.find(key);
+    if (it != gm->derived.end()) return GaugeView{it->second.first, stride};
+    const size_t bytes = gauge_bytes(prec, recon, stride);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *st = fail(QCD_ERR_OOM, "gauge copy: cudaMalloc(%zu) failed", bytes);
+        return GaugeView{nullptr, stride};
+    }
+    const GaugeView dst{p, stride}, src{g->data, stride};
+    cudaError_t e = launch_gauge_convert(dst, prec, recon, src, g->prec, g->recon, g->lat->geom, s);
+    if (e != cudaSuccess) {
+        cudaFree(p);
+        *st = check_cuda(e, "gauge copy");
+        return GaugeView{nullptr, stride};
+    }
+    gm->derived[key] = {p, bytes};
+    return dst;
+}
+
+// ----------------------------------------------------------------- hop
+
+Coef coef_twist(double b)
+{
+    Coef c;
+    c.c[0][0] = 1.0;
+    c.c[0][1] = b;
+    c.c[1][0] = 1.0;
+    c.c[1][1] = -b;
+    return c;
+}
+Coef coef_twist_inv(double b)
+{
+    const double n = 1.0 / (1.0 + b * b);
+    Coef c;
+    c.c[0][0] = n;
+    c.c[0][1] = -b * n;
+    c.c[1][0] = n;
+    c.c[1][1] = b * n;
+    return c;
+}
+Coef coef_scale(Coef c, double s)
+{
+    for (auto &k : c.c)
+        for (double &v : k) v *= s;
+    return c;
+}
+Coef coef_real(double s)
+{
+    Coef c;
+    c.c[0][0] = c.c[1][0] = s;
+    c.c[0][1] = c.c[1][1] = 0.0;
+    return c;
+}
+
+cudaError_t launch_dslash_f64(int recon, const DslashLaunch &a, cudaStream_t s);
+cudaError_t launch_dslash_f32(int recon, const DslashLaunch &a, cudaStream_t s);
+cudaError_t launch_dslash_f16(int recon, const DslashLaunch &a, cudaStream_t s);
+cudaError_t launch_dslash_bf16(int recon, const DslashLaunch &a, cudaStream_t s);
+
+cudaError_t launch_dslash(int prec, int recon, const DslashLaunch &a, cudaStream_t s)
+{
+    switch (prec) {
+    case QCD_PREC_F64: return launch_dslash_f64(recon, a, s);
+    case QCD_PREC_F32: return launch_dslash_f32(recon, a, s);
+    case QCD_PREC_F16: return launch_dslash_f16(recon, a, s);
+    case QCD_PREC_BF16: return launch_dslash_bf16(recon, a, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t hop(const qcd_lattice *lat, const GaugeView &U, int recon, const HopArgs &h, cudaStream_t s)
+{
+    DslashLaunch a;
+    memset(&a, 0, sizeof(a));
+    a.g = lat->geom;
+    a.out_parity = h.out_parity;
+    a.both = h.both ? 1 : 0;
+    a.dagger = h.dagger;
+    a.U = U;
+    if (h.both) {
+        for (int p = 0; p < 2; ++p) {
+            a.out[p] = h.out->hv[p];
+            a.in[p] = h.in->hv[1 - p];
+            if (h.y) a.y[p] = h.y->hv[p];
+        }
+    } else {
+        const int p = h.out_parity;
+        a.out[p] = h.out->hv[0];
+        a.in[p] = h.in->hv[0];
+        if (h.y) a.y[p] = h.y->hv[0];
+    }
+    memcpy(a.cy, h.cy.c, sizeof(a.cy));
+    memcpy(a.cd, h.cd.c, sizeof(a.cd));
+    if (h.plain)
+        a.epi = EPI_PLAIN;
+    else if (!h.y)
+        a.epi = h.twisted ? EPI_CPLX_D : EPI_REAL_D;
+    else
+        a.epi = h.twisted ? EPI_CPLX_YD : EPI_REAL_YD;
+    a.reduce = h.reduce;
+    a.red = reduction_of(lat);
+    a.fin = h.fin;
+    a.state = lat->state;
+    a.red_out = lat->red_out;
+    a.check_status = h.check_status;
+    return launch_dslash(h.out->prec, recon, a, s);
+}
+
+}  // namespace qcd
+
+using namespace qcd;
+
+// =================================================================== C ABI
+
+extern "C" {
+
+const char *qcd_status_string(qcd_status s)
+{
+    switch (s) {
+    case QCD_OK: return "QCD_OK";
+    case QCD_ERR_INVALID_ARG: return "QCD_ERR_INVALID_ARG";
+    case QCD_ERR_OOM: return "QCD_ERR_OOM";
+    case QCD_ERR_CUDA: return "QCD_ERR_CUDA";
+    case QCD_ERR_NOT_CONVERGED: return "QCD_ERR_NOT_CONVERGED";
+    case QCD_ERR_BREAKDOWN: return "QCD_ERR_BREAKDOWN";
+    case QCD_ERR_TIMEOUT: return "QCD_ERR_TIMEOUT";
+    default: return "QCD_ERR_UNKNOWN";
+    }
+}
+
+const char *qcd_last_error(void) { return g_err; }
+
+const char *qcd_version(void) { return "libqcd 0.1 (sm_103a)"; }
+
+qcd_status qcd_stream_sync(void *stream)
+{
+    return check_cuda(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)), "stream_sync");
+}
+
+qcd_status qcd_lattice_create(const int dims[4], int t_bc, qcd_lattice **out)
+{
+    if (!dims || !out) return fail(QCD_ERR_INVALID_ARG, "lattice_create: NULL argument");
+    *out = nullptr;
+    if (t_bc != 1 && t_bc != -1) return fail(QCD_ERR_INVALID_ARG, "lattice_create: t_bc must be +1 or -1");
+    uint64_t V = 1;
+    int lmax = 0;
+    for (int mu = 0; mu < 4; ++mu) {
+        if (dims[mu] < 2 || dims[mu] % 2) return fail(QCD_ERR_INVALID_ARG, "lattice_create: dims[%d] = %d must be even and >= 2", mu, dims[mu]);
+        V *= (uint64_t)dims[mu];
+        lmax = dims[mu] > lmax ? dims[mu] : lmax;
+    }
+    const uint64_t h = V / 2;
+    // 32-bit site indices and the exactness bound of FastDiv (n * d < 2^32)
+    if (V >= (1ull << 31) || h * (uint64_t)lmax >= (1ull << 32))
+        return fail(QCD_ERR_INVALID_ARG, "lattice_create: volume too large");
+    qcd_lattice *lat = new (std::nothrow) qcd_lattice();
+    if (!lat) return fail(QCD_ERR_OOM, "lattice_create: host allocation");
+    memcpy(lat->dims, dims, sizeof(lat->dims));
+    lat->t_bc = t_bc;
+    cudaGetDevice(&lat->device);
+    Geom &g = lat->geom;
+    for (int mu = 0; mu < 4; ++mu) g.L[mu] = dims[mu];
+    g.Lxh = dims[0] / 2;
+    g.h = (int)h;
+    g.sy = g.Lxh;
+    g.sz = g.Lxh * dims[1];
+    g.st = g.Lxh * dims[1] * dims[2];
+    g.dx = make_fastdiv(g.Lxh);
+    g.dy = make_fastdiv(dims[1]);
+    g.dz = make_fastdiv(dims[2]);
+    g.tbc = (double)t_bc;
+    lat->h = (int)h;
+    lat->stride = (int)((h + 63) / 64 * 64);
+    lat->red_cap = 2 * ((size_t)site_blocks((int)V) + 64);
+    cudaError_t e = cudaMalloc(&lat->red_partials, lat->red_cap * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&lat->red_counter, 64);
+    if (e == cudaSuccess) e = cudaMalloc(&lat->red_out, 8 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&lat->state, sizeof(CgState));
+    if (e == cudaSuccess) e = cudaMallocHost(&lat->state_host, sizeof(CgState));
+    if (e == cudaSuccess) e = cudaMemset(lat->red_counter, 0, 64);
+    if (e == cudaSuccess) e = cudaMemset(lat->state, 0, sizeof(CgState));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        qcd_status st = check_cuda(e, "lattice_create");
+        qcd_lattice_destroy(lat);
+        return st;
+    }
+    *out = lat;
+    return QCD_OK;
+}
+
+void qcd_lattice_destroy(qcd_lattice *lat)
+{
+    if (!lat) return;
+    cudaDeviceSynchronize();
+    cudaFree(lat->red_partials);
+    cudaFree(lat->red_counter);
+    cudaFree(lat->red_out);
+    cudaFree(lat->state);
+    if (lat->state_host) cudaFreeHost(lat->state_host);
+    for (auto &kv : lat->ws) cudaFree(kv.second.first);
+    delete lat;
+}
+
+qcd_status qcd_gauge_create(const qcd_lattice *lat, qcd_prec prec, qcd_recon recon, qcd_gauge **out)
+{
+    if (!lat || !out) return fail(QCD_ERR_INVALID_ARG, "gauge_create: NULL argument");
+    *out = nullptr;
+    if (!valid_prec(prec) || !valid_recon(recon)) return fail(QCD_ERR_INVALID_ARG, "gauge_create: bad prec/recon");
+    qcd_gauge *g = new (std::nothrow) qcd_gauge();
+    if (!g) return fail(QCD_ERR_OOM, "gauge_create: host allocation");
+    g->lat = lat;
+    g->prec = prec;
+    g->recon = recon;
+    g->bytes = gauge_bytes(prec, recon, lat->stride);
+    if (cudaMalloc(&g->data, g->bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete g;
+        return fail(QCD_ERR_OOM, "gauge_create: cudaMalloc(%zu) failed", gauge_bytes(prec, recon, lat->stride));
+    }
+    cudaMemset(g->data, 0, g->bytes);
+    *out = g;
+    return QCD_OK;
+}
+
+static void drop_derived(qcd_gauge *g)
+{
+    for (auto &kv : g->derived) cudaFree(kv.second.first);
+    g->derived.clear();
+}
+
+qcd_status qcd_gauge_upload(qcd_gauge *g, const double *host, void *stream)
+{
+    if (!g || !host) return fail(QCD_ERR_INVALID_ARG, "gauge_upload: NULL argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t bytes = (size_t)g->lat->h * 2 * 4 * 9 * 16;
+    if (!g->derived.empty()) {
+        cudaStreamSynchronize(s);
+        drop_derived(g);
+    }
+    void *stage = nullptr;
+    cudaError_t e = cudaMallocAsync(&stage, bytes, s);
+    if (e != cudaSuccess) return check_cuda(e, "gauge_upload: staging");
+    e = cudaMemcpyAsync(stage, host, bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = launch_gauge_pack(GaugeView{g->data, g->lat->stride}, g->prec, g->recon, static_cast<const double2 *>(stage),
+                              g->lat->geom, s);
+    cudaError_t e2 = cudaFreeAsync(stage, s);
+    if (e == cudaSuccess) e = e2;
+    return check_cuda(e, "gauge_upload");
+}
+
+qcd_status qcd_gauge_prepare(qcd_gauge *g, qcd_prec prec, qcd_recon recon, void *stream)
+{
+    if (!g) return fail(QCD_ERR_INVALID_ARG, "gauge_prepare: NULL argument");
+    if (!valid_prec(prec) || !valid_recon(recon)) return fail(QCD_ERR_INVALID_ARG, "gauge_prepare: bad prec/recon");
+    qcd_status st;
+    gauge_view(g, prec, recon, static_cast<cudaStream_t>(stream), &st);
+    return st;
+}
+
+void qcd_gauge_destroy(qcd_gauge *g)
+{
+    if (!g) return;
+    cudaDeviceSynchronize();
+    drop_derived(g);
+    cudaFree(g->data);
+    delete g;
+}
+
+qcd_status qcd_spinor_bytes(const qcd_lattice *lat, qcd_parity parity, qcd_prec prec, size_t *data_bytes,
+                            size_t *norm_bytes)
+{
+    if (!lat || !data_bytes || !norm_bytes) return fail(QCD_ERR_INVALID_ARG, "spinor_bytes: NULL argument");
+    if (!valid_prec(prec) || parity < 0 || parity > 2) return fail(QCD_ERR_INVALID_ARG, "spinor_bytes: bad prec/parity");
+    const int nh = parity == QCD_PARITY_FULL ? 2 : 1;
+    *data_bytes = nh * spinor_half_bytes(prec, lat->stride);
+    *norm_bytes = nh * spinor_half_norm_bytes(prec, lat->stride);
+    return QCD_OK;
+}
+
+static qcd_spinor *new_spinor(const qcd_lattice *lat, qcd_parity parity, qcd_prec prec)
+{
+    qcd_spinor *s = new (std::nothrow) qcd_spinor();
+    if (!s) return nullptr;
+    s->lat = lat;
+    s->parity = parity;
+    s->prec = prec;
+    s->half_data_bytes = spinor_half_bytes(prec, lat->stride);
+    s->half_norm_bytes = spinor_half_norm_bytes(prec, lat->stride);
+    return s;
+}
+
+qcd_status qcd_spinor_create(const qcd_lattice *lat, qcd_parity parity, qcd_prec prec, qcd_spinor **out)
+{
+    if (!lat || !out) return fail(QCD_ERR_INVALID_ARG, "spinor_create: NULL argument");
+    *out = nullptr;
+    if (!valid_prec(prec) || parity < 0 || parity > 2) return fail(QCD_ERR_INVALID_ARG, "spinor_create: bad prec/parity");
+    qcd_spinor *s = new_spinor(lat, parity, prec);
+    if (!s) return fail(QCD_ERR_OOM, "spinor_create: host allocation");
+    const int nh = parity == QCD_PARITY_FULL ? 2 : 1;
+    cudaError_t e = cudaMalloc(&s->data, nh * s->half_data_bytes);
+    if (e == cudaSuccess && s->half_norm_bytes) e = cudaMalloc(reinterpret_cast<void **>(&s->norm), nh * s->half_norm_bytes);
+    if (e == cudaSuccess) e = cudaMemset(s->data, 0, nh * s->half_data_bytes);
+    if (e == cudaSuccess && s->norm) e = cudaMemset(s->norm, 0, nh * s->half_norm_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(s->data);
+        cudaFree(s->norm);
+        delete s;
+        return fail(QCD_ERR_OOM, "spinor_create: cudaMalloc failed");
+    }
+    *out = s;
+    return QCD_OK;
+}
+
+qcd_status qcd_spinor_wrap_device(const qcd_lattice *lat, qcd_parity parity, qcd_prec prec, void *data, void *norm,
+                                  qcd_spinor **out)
+{
+    if (!lat || !out || !data) return fail(QCD_ERR_INVALID_ARG, "spinor_wrap_device: NULL argument");
+    *out = nullptr;
+    if (!valid_prec(prec) || parity < 0 || parity > 2) return fail(QCD_ERR_INVALID_ARG, "spinor_wrap_device: bad prec/parity");
+    if (prec == QCD_PREC_F16 && !norm) return fail(QCD_ERR_INVALID_ARG, "spinor_wrap_device: F16 needs a norm buffer");
+    if ((reinterpret_cast<uintptr_t>(data) & 255) || (reinterpret_cast<uintptr_t>(norm) & 255))
+        return fail(QCD_ERR_INVALID_ARG, "spinor_wrap_device: buffers must be 256-byte aligned");
+    qcd_spinor *s = new_spinor(lat, parity, prec);
+    if (!s) return fail(QCD_ERR_OOM, "spinor_wrap_device: host allocation");
+    s->data = data;
+    s->norm = prec == QCD_PREC_F16 ? static_cast<float *>(norm) : nullptr;
+    s->owns = false;
+    *out = s;
+    return QCD_OK;
+}
+
+void qcd_spinor_destroy(qcd_spinor *s)
+{
+    if (!s) return;
+    if (s->owns) {
+        cudaDeviceSynchronize();
+        cudaFree(s->data);
+        cudaFree(s->norm);
+    }
+    delete s;
+}
+
+qcd_status qcd_spinor_upload(qcd_spinor *s, const double *host, void *stream)
+{
+    if (!s || !host) return fail(QCD_ERR_INVALID_ARG, "spinor_upload: NULL argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int nh = s->parity == QCD_PARITY_FULL ? 2 : 1;
+    const size_t bytes = (size_t)nh * s->lat->h * 192;
+    void *stage = workspace(s->lat, "staging", bytes);
+    if (!stage) return fail(QCD_ERR_OOM, "spinor_upload: staging");
+    cudaError_t e = cudaMemcpyAsync(stage, host, bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = launch_spinor_pack(view_of(s), s->parity, static_cast<const double2 *>(stage), s->lat->geom, st);
+    return check_cuda(e, "spinor_upload");
+}
+
+qcd_status qcd_spinor_download(const qcd_spinor *s, double *host, void *stream)
+{
+    if (!s || !host) return fail(QCD_ERR_INVALID_ARG, "spinor_download: NULL argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int nh = s->parity == QCD_PARITY_FULL ? 2 : 1;
+    const size_t bytes = (size_t)nh * s->lat->h * 192;
+    void *stage = workspace(s->lat, "staging", bytes);
+    if (!stage) return fail(QCD_ERR_OOM, "spinor_download: staging");
+    cudaError_t e = launch_spinor_unpack(static_cast<double2 *>(stage), view_of(s), s->parity, s->lat->geom, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host, stage, bytes, cudaMemcpyDeviceToHost, st);
+    return check_cuda(e, "spinor_download");
+}
+
+qcd_status qcd_spinor_zero(qcd_spinor *s, void *stream)
+{
+    if (!s) return fail(QCD_ERR_INVALID_ARG, "spinor_zero: NULL argument");
+    return check_cuda(launch_zero(view_of(s), static_cast<cudaStream_t>(stream)), "spinor_zero");
+}
+
+qcd_status qcd_spinor_convert(qcd_spinor *dst, const qcd_spinor *src, void *stream)
+{
+    if (!dst || !src) return fail(QCD_ERR_INVALID_ARG, "spinor_convert: NULL argument");
+    if (dst->lat != src->lat || dst->parity != src->parity)
+        return fail(QCD_ERR_INVALID_ARG, "spinor_convert: lattice or parity differ");
+    return check_cuda(launch_convert(view_of(dst), view_of(src), static_cast<cudaStream_t>(stream)), "spinor_convert");
+}
+
+qcd_status qcd_spinor_norm2(const qcd_spinor *s, double *result_device, void *stream)
+{
+    if (!s || !result_device) return fail(QCD_ERR_INVALID_ARG, "spinor_norm2: NULL argument");
+    return check_cuda(launch_norm2(view_of(s), reduction_of(s->lat), FIN_STORE, s->lat->state, result_device,
+                                   static_cast<cudaStream_t>(stream)),
+                      "spinor_norm2");
+}
+
+qcd_status qcd_apply_dslash(const qcd_gauge *g, qcd_spinor *out, const qcd_spinor *in, int dagger, void *stream)
+{
+    if (!g || !out || !in) return fail(QCD_ERR_INVALID_ARG, "apply_dslash: NULL argument");
+    if (out->lat != g->lat || in->lat != g->lat) return fail(QCD_ERR_INVALID_ARG, "apply_dslash: lattices differ");
+    if (out->prec != in->prec) return fail(QCD_ERR_INVALID_ARG, "apply_dslash: precisions differ");
+    if (out == in || out->data == in->data) return fail(QCD_ERR_INVALID_ARG, "apply_dslash: out aliases in");
+    const bool both = out->parity == QCD_PARITY_FULL && in->parity == QCD_PARITY_FULL;
+    if (!both && !(out->parity != QCD_PARITY_FULL && in->parity == 1 - out->parity))
+        return fail(QCD_ERR_INVALID_ARG, "apply_dslash: parities must be (EVEN, ODD), (ODD, EVEN) or (FULL, FULL)");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    qcd_status st;
+    GaugeView U = gauge_view(g, out->prec, g->recon, s, &st);
+    if (st != QCD_OK) return st;
+    const FieldView fo = view_of(out), fi = view_of(in);
+    HopArgs h{};
+    h.out = &fo;
+    h.in = &fi;
+    h.y = nullptr;
+    h.out_parity = both ? 0 : out->parity;
+    h.both = both;
+    h.dagger = dagger ? 1 : 0;
+    h.plain = true;
+    h.fin = FIN_STORE;
+    return check_cuda(hop(g->lat, U, g->recon, h, s), "apply_dslash");
+}
+
+qcd_status qcd_apply_M(const qcd_gauge *g, qcd_spinor *out, const qcd_spinor *in, double kappa, double mu, int eo,
+                       int dagger, void *stream)
+{
+    if (!g || !out || !in) return fail(QCD_ERR_INVALID_ARG, "apply_M: NULL argument");
+    if (out->lat != g->lat || in->lat != g->lat) return fail(QCD_ERR_INVALID_ARG, "apply_M: lattices differ");
+    if (out->prec != in->prec) return fail(QCD_ERR_INVALID_ARG, "apply_M: precisions differ");
+    if (out == in || out->data == in->data) return fail(QCD_ERR_INVALID_ARG, "apply_M: out aliases in");
+    if (eo && (out->parity != QCD_PARITY_EVEN || in->parity != QCD_PARITY_EVEN))
+        return fail(QCD_ERR_INVALID_ARG, "apply_M: eo = 1 needs EVEN fields");
+    if (!eo && (out->parity != QCD_PARITY_FULL || in->parity != QCD_PARITY_FULL))
+        return fail(QCD_ERR_INVALID_ARG, "apply_M: eo = 0 needs FULL fields");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    qcd_status st;
+    GaugeView U = gauge_view(g, out->prec, g->recon, s, &st);
+    if (st != QCD_OK) return st;
+    const double a = 2.0 * kappa * mu, b = dagger ? -a : a;
+    const bool tw = a != 0.0;
+    const FieldView fo = view_of(out), fi = view_of(in);
+    HopArgs h{};
+    h.dagger = dagger ? 1 : 0;
+    h.fin = FIN_STORE;
+    if (!eo) {
+        h.out = &fo;
+        h.in = &fi;
+        h.y = &fi;
+        h.both = true;
+        h.cy = coef_twist(b);
+        h.cd = coef_real(-kappa);
+        h.twisted = tw;
+        return check_cuda(hop(g->lat, U, g->recon, h, s), "apply_M");
+    }
+    const FieldView t = ws_field(g->lat, "applyM_t", 1, out->prec);
+    if (!t.hv[0].data) return fail(QCD_ERR_OOM, "apply_M: workspace");
+    h.out = &t;
+    h.in = &fi;
+    h.y = nullptr;
+    h.out_parity = 1;
+    h.plain = !tw;
+    h.twisted = tw;
+    h.cd = coef_twist_inv(b);
+    cudaError_t e = hop(g->lat, U, g->recon, h, s);
+    if (e != cudaSuccess) return check_cuda(e, "apply_M");
+    HopArgs h2{};
+    h2.dagger = h.dagger;
+    h2.fin = FIN_STORE;
+    h2.out = &fo;
+    h2.in = &t;
+    h2.y = &fi;
+    h2.out_parity = 0;
+    h2.cy = coef_twist(b);
+    h2.cd = coef_real(-kappa * kappa);
+    h2.twisted = tw;
+    return check_cuda(hop(g->lat, U, g->recon, h2, s), "apply_M");
+}
+
+}  // extern "C"

@@ -1,0 +1,95 @@
+// Handle structures behind the opaque C types (internal).
+#pragma once
+
+#include <map>
+#include <string>
+
+#include "qcd_ops.h"
+
+struct qcd_lattice {
+    int dims[4];
+    int t_bc;
+    int device;
+    qcd::Geom geom;
+    int h;       // sites per parity
+    int stride;  // padded sites per plane
+
+    // Scratch shared by the calls on this lattice (stream-ordered use).
+    double *red_partials = nullptr;  // reduction partials
+    size_t red_cap = 0;              // doubles
+    unsigned *red_counter = nullptr; // ticket counter (zero between kernels)
+    double *red_out = nullptr;       // FIN_STORE results (8 doubles)
+    qcd::CgState *state = nullptr;   // device CG state
+    qcd::CgState *state_host = nullptr;  // pinned mirror
+    // Named workspace buffers (staging, solver fields), grown on demand.
+    mutable std::map<std::string, std::pair<void *, size_t>> ws;
+};
+
+struct qcd_gauge {
+    const qcd_lattice *lat;
+    int prec, recon;
+    void *data = nullptr;
+    size_t bytes = 0;
+    // Copies in other (prec, recon) formats, keyed by prec * 100 + recon.
+    std::map<int, std::pair<void *, size_t>> derived;
+};
+
+struct qcd_spinor {
+    const qcd_lattice *lat;
+    int parity;  // qcd_parity
+    int prec;
+    void *data = nullptr;
+    float *norm = nullptr;
+    size_t half_data_bytes = 0;  // bytes of one half field's planes
+    size_t half_norm_bytes = 0;
+    bool owns = true;
+};
+
+namespace qcd {
+
+// Per-thread error message for qcd_last_error().
+qcd_status fail(qcd_status code, const char *fmt, ...);
+qcd_status check_cuda(cudaError_t e, const char *what);
+
+size_t spinor_half_bytes(int prec, int stride);
+size_t spinor_half_norm_bytes(int prec, int stride);
+size_t gauge_bytes(int prec, int recon, int stride);
+
+// Workspace buffer `name` of at least `bytes` on the lattice.
+void *workspace(const qcd_lattice *lat, const std::string &name, size_t bytes);
+
+// Views.
+FieldView view_of(const qcd_spinor *s);
+FieldView view_half(const qcd_spinor *s, int half);  // half of a FULL field
+FieldView ws_field(const qcd_lattice *lat, const std::string &name, int nh, int prec);
+GaugeView gauge_view(const qcd_gauge *g, int prec, int recon, cudaStream_t s, qcd_status *st);
+Reduction reduction_of(const qcd_lattice *lat);
+
+cudaError_t launch_dslash(int prec, int recon, const DslashLaunch &a, cudaStream_t s);
+
+// Chiral coefficients of (1 + i b gamma_5) and of its inverse.
+struct Coef {
+    double c[2][2];  // [chirality][re, im]
+};
+Coef coef_twist(double b);
+Coef coef_twist_inv(double b);
+Coef coef_scale(Coef c, double s);
+Coef coef_real(double s);
+
+// Dslash launch on FieldViews: out (parity p) = cy .* y + cd .* D in.
+// `y` may be null.  With both = true, out, in and y are FULL fields.
+struct HopArgs {
+    const FieldView *out, *in, *y;
+    int out_parity;
+    bool both;
+    int dagger;
+    Coef cy, cd;
+    bool plain;      // out = D in (cy, cd ignored)
+    bool twisted;    // complex chiral coefficients
+    bool reduce;
+    FinalizeKind fin;
+    bool check_status;
+};
+cudaError_t hop(const qcd_lattice *lat, const GaugeView &U, int recon, const HopArgs &h, cudaStream_t s);
+
+}  // namespace qcd

