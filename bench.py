@@ -1,0 +1,452 @@
+"""Benchmark: even-odd Wilson CG solves/s and Dslash bandwidth on GB300.
+
+Step = one FP64 even-odd CG solve of M x = b to relative residual 1e-10 on
+the 24^3 x 8 workload (kappa = 0.155, near-unit SU(3) links exp(0.2 i H),
+Gaussian source): source preparation, CG on Mhat^dag Mhat, odd-site
+reconstruction and the FP64 true residual, all on the GPU through the C ABI.
+Inputs are resident in HBM; L2 is flushed (a 512 MiB write, > the 129 MB
+L2) before every timed solve.  The same JSON line also reports:
+
+  mixed_vs_fp64  mixed-precision (FP16 storage + FP32 inner, FP64 reliable
+                 updates) against FP64 solves/s at the same 1e-10, on this
+                 workload and on 32^3x8 / 48^3x12 twisted mass (mu = 0.01,
+                 kappa = 0.16, reconstruct-12 inner links);
+  dslash_sweep   achieved GB/s and fraction of the measured HBM peak of the
+                 even-odd Dslash over five volumes and storage formats;
+  roofline       the dominant kernel of the step (the FP64 Dslash), timed
+                 with CUDA events on its stream inside the timed region;
+  cpu_baseline   the FP64 CPU oracle on this host's cores, a bounded sample.
+
+--impl reference times the CPU oracle as the reference arm.
+With torchrun (N > 1) every rank solves its own copy of the problem
+(independent solves: replicas, weak scaling, no collective on the path).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "eo-Wilson Dslash GB/s & %HBM roofline; mixed vs FP64 CG solves/s at 1e-10"
+WORKLOAD = "24^3x8"
+TOL = 1e-10
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x FP64 FMA/clk x 2 flop x max clock
+HBM_FALLBACK_GBS = 6800.0
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+        self.dev = str(device_index)
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            self.dev = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+        except Exception:
+            pass
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.dev, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        sm = [r[0] for r in rows]
+        loaded = [v for v in sm if v >= 0.5 * max(sm)] or sm
+        return {"sm_mhz": float(np.median(loaded)), "sm_max_mhz": float(max(r[1] for r in rows)),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ problem
+
+class Problem:
+    def __init__(self, qcd, name, mu=None, kappa=None, gauge_recon=18):
+        from paper_1411_5219_gb300 import synthetic as syn
+        import torch
+        w = syn.WORKLOADS[name]
+        self.name, self.dims = name, w["dims"]
+        self.kappa = w["kappa"] if kappa is None else kappa
+        self.mu = w["mu"] if mu is None else mu
+        self.lat = qcd.Lattice(self.dims, -1)
+        U = syn.gauge_field(self.dims, w["eps"], w["seed"])
+        self.gauge = qcd.Gauge(self.lat, "f64", gauge_recon)
+        self.gauge.upload(U)
+        self.U = U
+        b = syn.gaussian_spinor(self.dims, w["seed"])
+        self.b_np = b
+        self.b_host = torch.from_numpy(b.copy()).pin_memory()
+        self.x_host = torch.empty_like(self.b_host).pin_memory()
+        self.b = qcd.Spinor(self.lat, "full", "f64")
+        self.x = qcd.Spinor(self.lat, "full", "f64")
+        self.b.upload(b)
+        qcd.stream_sync()
+        self.volume = self.lat.volume
+
+    def solve(self, qcd, inner="f64", recon=12, eo=True, normal=False):
+        return qcd.solve_cg(self.gauge, self.x, self.b, self.kappa, self.mu, tol=TOL, eo=eo, normal=normal,
+                            inner_prec=inner, inner_recon=recon, reliable_delta=0.1)
+
+
+def flush_l2(buf):
+    buf.add_(1)
+
+
+def timed_steps(torch, fn, k, flush):
+    """Event-timed steps with an untimed L2 flush before each; returns seconds per step."""
+    s = torch.cuda.current_stream()
+    evs = []
+    for _ in range(k):
+        flush_l2(flush)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        fn()
+        e1.record(s)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) * 1e-3 for a, b in evs]
+
+
+# ------------------------------------------------------------------ extras
+
+def dslash_sweep(qcd, torch, flush, hbm, reps=20):
+    from paper_1411_5219_gb300 import synthetic as syn
+    out = {}
+    fmts = [("f64", 18, 1536), ("f64", 12, 1152), ("f32", 12, 576), ("f16", 12, 296), ("bf16", 12, 288)]
+    for dims in syn.SWEEP_VOLUMES:
+        lat = qcd.Lattice(dims, -1)
+        U = syn.gauge_field(dims, 0.2, 1002)
+        psi = syn.gaussian_spinor(dims, 5)
+        h = lat.volume // 2
+        row = {}
+        for recon in (18, 12):
+            g = qcd.Gauge(lat, "f64", recon)
+            g.upload(U)
+            for prec, rc, bps in fmts:
+                if rc != recon:
+                    continue
+                si, so = qcd.Spinor(lat, "odd", prec), qcd.Spinor(lat, "even", prec)
+                si.upload(syn.to_half(psi, 1))
+                fn = lambda: qcd.apply_dslash(g, so, si)  # noqa: E731
+                for _ in range(3):
+                    fn()
+                ts = timed_steps(torch, fn, reps, flush)
+                t = float(np.median(ts))
+                gbs = h * bps / t / 1e9
+                row[f"{prec}_r{recon}"] = {"us": round(t * 1e6, 2), "GB_s": round(gbs, 1),
+                                           "frac_hbm": round(gbs / hbm, 3),
+                                           "TFLOP_s": round(h * 1320 / t / 1e12, 3)}
+            del g
+        out["x".join(map(str, dims))] = row
+        del lat
+    return out
+
+
+def cpu_oracle_sample(target_s=15.0):
+    """Time FP64 oracle CG iterations on this host's cores (bounded sample)."""
+    import oracle
+    from paper_1411_5219_gb300 import synthetic as syn
+    w = syn.WORKLOADS[WORKLOAD]
+    U = syn.gauge_field(w["dims"], w["eps"], w["seed"])
+    b = syn.gaussian_spinor(w["dims"], w["seed"])
+    be = syn.to_half(b, 0)
+    t0 = time.time()
+    oracle.cg_eo_sample(U, be, w["kappa"], w["mu"], iters=2)
+    t_it = (time.time() - t0) / 2
+    n = int(max(2, min(200, target_s / max(t_it, 1e-6))))
+    t0 = time.time()
+    oracle.cg_eo_sample(U, be, w["kappa"], w["mu"], iters=n)
+    t_it = (time.time() - t0) / n
+    golden = os.path.join(ROOT, "tests", "golden", "oracle_cg_iterations.json")
+    with open(golden) as f:
+        iters = json.load(f)[WORKLOAD]["iterations"]
+    return {"iters_sampled": n, "s_per_iter": t_it, "iters_per_solve": iters,
+            "solves_s": 1.0 / (t_it * iters), "cores": oracle.get_threads(), "sample_s": t_it * n}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1411_5219_gb300 import synthetic as syn
+    w = syn.WORKLOADS[WORKLOAD]
+    U = syn.gauge_field(w["dims"], w["eps"], w["seed"])
+    be = syn.to_half(syn.gaussian_spinor(w["dims"], w["seed"]), 0)
+    with open(os.path.join(ROOT, "tests", "golden", "oracle_cg_iterations.json")) as f:
+        iters = json.load(f)[WORKLOAD]["iterations"]
+    n_it = args.ref_iters
+    for _ in range(args.warmup):
+        oracle.cg_eo_sample(U, be, w["kappa"], w["mu"], iters=1)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.time()
+        oracle.cg_eo_sample(U, be, w["kappa"], w["mu"], iters=n_it)
+        ts.append(time.time() - t0)
+    t_solve = float(np.mean(ts)) / n_it * iters
+    value = 1.0 / t_solve
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(ts)) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "24^3x8 even-odd Wilson kappa=0.155, eps=0.2 links, Gaussian source, "
+                                   "FP64 CG to 1e-10", "lattice": list(w["dims"]), "kappa": w["kappa"],
+                       "tol": TOL},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": oracle.get_threads(), "kind": "oracle",
+                             "sample": f"each step = {n_it} FP64 oracle CG iterations of the 24^3x8 even-odd "
+                                       f"system, scaled by the oracle's {iters} iterations per solve"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def dslash_only(args):
+    """Launch D_eo `reps` times on one volume/format (for ncu), print timings."""
+    import torch
+    from paper_1411_5219_gb300 import qcd, synthetic as syn
+    dims = tuple(int(v) for v in args.dslash[0].split("x"))
+    prec, recon = args.dslash[1], int(args.dslash[2])
+    lat = qcd.Lattice(dims, -1)
+    g = qcd.Gauge(lat, "f64", recon)
+    g.upload(syn.gauge_field(dims, 0.2, 1002))
+    g.prepare(prec, recon)
+    si, so = qcd.Spinor(lat, "odd", prec), qcd.Spinor(lat, "even", prec)
+    si.upload(syn.to_half(syn.gaussian_spinor(dims, 5), 1))
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ts = timed_steps(torch, lambda: qcd.apply_dslash(g, so, si), args.reps, flush)
+    print(json.dumps({"dslash": args.dslash, "us": [round(t * 1e6, 2) for t in ts]}))
+    return 0
+
+
+# ------------------------------------------------------------------ main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-iters", type=int, default=10)
+    ap.add_argument("--no-extras", action="store_true", help="skip the mixed/sweep/CPU-baseline blocks")
+    ap.add_argument("--dslash", nargs=3, metavar=("DIMS", "PREC", "RECON"),
+                    help="only launch the even-odd Dslash (e.g. 48x48x48x12 f16 12), for profilers")
+    ap.add_argument("--reps", type=int, default=3)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.dslash:
+        return dslash_only(args)
+
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1411_5219_gb300 import qcd
+    qcd.lib()  # raises if libqcd.so is missing: there is no fallback path
+    hbm, hbm_kind = peaks()
+
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    prob = Problem(qcd, WORKLOAD)
+    for _ in range(args.warmup):
+        prob.solve(qcd)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    l0 = qcd.kernel_launches()
+    t_wall = time.time()
+    stats = []
+
+    def step():
+        _, st = prob.solve(qcd)
+        stats.append(st)
+
+    ts = timed_steps(torch, step, args.steps, flush)
+    t_wall = time.time() - t_wall
+    launches = qcd.kernel_launches() - l0
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    total = float(np.sum(ts))
+    if ws > 1:
+        t = torch.tensor([total], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total = float(t.item())
+    value = ws * args.steps / total
+    iters = [s["iterations"] for s in stats]
+    resid = max(s["true_rel_residual"] for s in stats)
+
+    # Dslash durations: the same K solves again with every hopping-kernel
+    # launch bracketed by CUDA events on the solver's stream (the solver then
+    # launches kernel by kernel instead of replaying its graph).
+    qcd.profile_begin()
+    tp = timed_steps(torch, lambda: prob.solve(qcd), args.steps, flush)
+    prof = qcd.profile_end()
+    d = prof["f64"]
+    achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else None
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "24^3x8 even-odd Wilson kappa=0.155, eps=0.2 links, Gaussian source, "
+                               "FP64 CG to 1e-10",
+                   "lattice": list(prob.dims), "kappa": prob.kappa, "tol": TOL, "parallelism": "replicas",
+                   "l2": "flushed before every timed solve (512 MiB write)"},
+        "iterations": int(np.median(iters)), "true_rel_residual": resid,
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "alu", "kernel": "dslash FP64 (D_eo/D_oe with fused epilogues) in the CG",
+                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS if achieved else None, "traffic": None,
+                     "launches": d["launches"], "avg_us": d["ms"] / max(d["launches"], 1) * 1e3,
+                     "achieved_GB_s": d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else None,
+                     "hbm_peak_GB_s": hbm,
+                     "profiled_pass_ms_per_step": float(np.mean(tp)) * 1e3,
+                     "peak_note": "FP64: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (an FMA probe measured 1.25)"},
+        "wall_s": t_wall,
+    }
+    if clk:
+        line["clocks"] = clk
+
+    extras = (ws == 1) and not args.no_extras and rank == 0
+    if extras:
+        # e2e through the public API with host buffers (pinned)
+        def e2e_step():
+            prob.b.upload(prob.b_host)
+            prob.solve(qcd)
+            prob.x.download(prob.x_host, sync=False)
+
+        te = timed_steps(torch, e2e_step, args.steps, flush)
+        nbytes = prob.volume * 192
+        line["e2e"] = {"value": args.steps / float(np.sum(te)), "unit": "solves/s",
+                       "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+        # mixed precision vs FP64
+        mixed = {}
+        x64 = prob.x.download()
+        tm = timed_steps(torch, lambda: stats.append(prob.solve(qcd, inner="f16", recon=12)[1]), args.steps, flush)
+        sm = stats[-1]
+        xm = prob.x.download()
+        qcd.profile_begin()
+        timed_steps(torch, lambda: prob.solve(qcd, inner="f16", recon=12), 2, flush)
+        f16d = qcd.profile_end()["f16"]
+        mixed["24^3x8 Wilson k=0.155"] = {
+            "fp64_solves_s": value, "mixed_f16_solves_s": args.steps / float(np.sum(tm)),
+            "ratio": (args.steps / float(np.sum(tm))) / value,
+            "fp64_iters": int(np.median(iters)), "mixed_iters": sm["iterations"],
+            "reliable_updates": sm["reliable_updates"], "mixed_true_rel_residual": sm["true_rel_residual"],
+            "mixed_rel_err_vs_fp64_x": float(np.linalg.norm(xm - x64) / np.linalg.norm(x64)),
+            "f16_dslash_GB_s": f16d["bytes"] / (f16d["ms"] * 1e-3) / 1e9 if f16d["ms"] else None,
+            "f16_dslash_frac_hbm": (f16d["bytes"] / (f16d["ms"] * 1e-3) / 1e9) / hbm if f16d["ms"] else None}
+        del prob
+        for name, reps in (("32^3x8", max(2, args.steps // 2)), ("48^3x12", 2)):
+            p = Problem(qcd, name)
+            p.solve(qcd)
+            p.solve(qcd, inner="f16")
+            st64, stm = [], []
+            t64 = timed_steps(torch, lambda: st64.append(p.solve(qcd)[1]), reps, flush)
+            xr = p.x.download()
+            tmx = timed_steps(torch, lambda: stm.append(p.solve(qcd, inner="f16", recon=12)[1]), reps, flush)
+            xm = p.x.download()
+            v64, vm = reps / float(np.sum(t64)), reps / float(np.sum(tmx))
+            mixed[f"{name} twisted mass k=0.16 mu=0.01"] = {
+                "fp64_solves_s": v64, "mixed_f16_solves_s": vm, "ratio": vm / v64,
+                "fp64_iters": st64[-1]["iterations"], "mixed_iters": stm[-1]["iterations"],
+                "reliable_updates": stm[-1]["reliable_updates"],
+                "fp64_true_rel_residual": st64[-1]["true_rel_residual"],
+                "mixed_true_rel_residual": stm[-1]["true_rel_residual"],
+                "mixed_rel_err_vs_fp64_x": float(np.linalg.norm(xm - xr) / np.linalg.norm(xr))}
+            del p
+        line["mixed_vs_fp64"] = mixed
+        # full-lattice 4^4 normal-equation solve
+        p4 = Problem(qcd, "4^4")
+        t4 = timed_steps(torch, lambda: p4.solve(qcd, eo=False, normal=True), args.steps, flush)
+        line["full_4x4_normal_solves_s"] = args.steps / float(np.sum(t4))
+        del p4
+        line["dslash_sweep"] = dslash_sweep(qcd, torch, flush, hbm)
+        line["dslash_sweep_note"] = (f"cold L2 (flushed before each launch); GB/s on compulsory bytes per "
+                                     f"output site; frac of {hbm_kind} HBM {hbm} GB/s")
+        try:
+            cb = cpu_oracle_sample()
+            line["cpu_baseline"] = {"value": cb["solves_s"], "unit": "solves/s", "cores": cb["cores"],
+                                    "kind": "oracle",
+                                    "sample": f"{cb['iters_sampled']} FP64 oracle CG iterations of the 24^3x8 "
+                                              f"even-odd system ({cb['sample_s']:.1f} s), scaled by the oracle's "
+                                              f"{cb['iters_per_solve']} iterations per solve"}
+        except Exception as e:  # the oracle is a baseline, not the product
+            line["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+                                    "sample": f"not run: {e}"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -201,6 +201,38 @@ typedef struct {
 qcd_status qcd_solve_cg(const qcd_gauge *g, qcd_spinor *x, const qcd_spinor *b, const qcd_solver_params *params,
                         qcd_solver_stats *stats, void *stream);
 
+/* ------------------------------------------------------------ measurement */
+
+/* The paper's kernel classes carry the number of FLOPs each kernel performs
+ * so that performance can be reported (Sec. 4), and it rates the Dslash by
+ * its achieved memory bandwidth (Sec. 1, Sec. 6).  Between
+ * qcd_profile_begin and qcd_profile_end every hopping-kernel launch is
+ * bracketed by CUDA events on its own stream, and its algorithmic traffic
+ * and flops are recorded:
+ *   bytes = sites * (8 links + 1 input spinor + 1 output spinor
+ *                    [+ 1 spinor y of the fused epilogue]),
+ *           in the storage precision (links at 18 or 12 reals; FP16
+ *           spinors include their 4-byte scale);
+ *   flops = 1320 per output site (projection, two SU(3) products and the
+ *           accumulation of 8 hops; the rebuilt third link row and the
+ *           epilogue are not counted).
+ * Entries are indexed by qcd_prec.  One profiling window at a time, from
+ * one host thread.  qcd_profile_end waits for the recorded events. */
+typedef struct {
+    long long launches;
+    double ms;     /* summed device time of the launches */
+    double bytes;  /* summed algorithmic bytes */
+    double flops;  /* summed algorithmic flops */
+    double sites;  /* summed output sites */
+} qcd_profile_entry;
+typedef struct {
+    qcd_profile_entry prec[4];
+} qcd_profile;
+qcd_status qcd_profile_begin(void);
+qcd_status qcd_profile_end(qcd_profile *out);
+/* Number of CUDA kernels this library has launched since it was loaded. */
+unsigned long long qcd_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,15 +1,61 @@
 // C ABI of libqcd: handles, host<->device transfer, operator application.
 // Declarations and argument conventions are in include/qcd.h.
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <vector>
 
 #include "qcd_handles.h"
 
 namespace qcd {
 
 static thread_local char g_err[512] = "";
+static std::atomic<unsigned long long> g_launches{0};
+
+void note_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+
+// ---- hopping-kernel profiling (qcd_profile_begin / qcd_profile_end)
+struct ProfRec {
+    cudaEvent_t e0, e1;
+    int prec;
+    double bytes, flops, sites;
+};
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static std::vector<ProfRec> g_prof;
+static std::vector<cudaEvent_t> g_event_pool;
+
+bool profiling_active() { return g_prof_on; }
+
+static cudaEvent_t pool_event()
+{
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+static double spinor_site_bytes(int prec)
+{
+    switch (prec) {
+    case QCD_PREC_F64: return 192;
+    case QCD_PREC_F32: return 96;
+    case QCD_PREC_F16: return 52;
+    default: return 48;
+    }
+}
+static double link_bytes(int prec, int recon)
+{
+    const double w = prec == QCD_PREC_F64 ? 8 : prec == QCD_PREC_F32 ? 4 : 2;
+    return w * recon;
+}
 
 qcd_status fail(qcd_status code, const char *fmt, ...)
 {
@@ -232,7 +278,25 @@ cudaError_t hop(const qcd_lattice *lat, const GaugeView &U, int recon, const Hop
     a.state = lat->state;
     a.red_out = lat->red_out;
     a.check_status = h.check_status;
-    return launch_dslash(h.out->prec, recon, a, s);
+    const bool prof = g_prof_on;
+    if (!prof) {
+        note_launches();
+        return launch_dslash(h.out->prec, recon, a, s);
+    }
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    ProfRec r;
+    r.e0 = pool_event();
+    r.e1 = pool_event();
+    r.prec = h.out->prec;
+    r.sites = (double)lat->h * (h.both ? 2 : 1);
+    r.bytes = r.sites * (8 * link_bytes(h.out->prec, recon) + (h.y ? 3 : 2) * spinor_site_bytes(h.out->prec));
+    r.flops = r.sites * 1320.0;
+    cudaEventRecord(r.e0, s);
+    note_launches();
+    cudaError_t e = launch_dslash(h.out->prec, recon, a, s);
+    cudaEventRecord(r.e1, s);
+    g_prof.push_back(r);
+    return e;
 }
 
 }  // namespace qcd
@@ -260,6 +324,43 @@ const char *qcd_status_string(qcd_status s)
 const char *qcd_last_error(void) { return g_err; }
 
 const char *qcd_version(void) { return "libqcd 0.1 (sm_103a)"; }
+
+unsigned long long qcd_kernel_launches(void) { return g_launches.load(); }
+
+qcd_status qcd_profile_begin(void)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (g_prof_on) return fail(QCD_ERR_INVALID_ARG, "profile_begin: a profiling window is already open");
+    g_prof.clear();
+    g_prof_on = true;
+    return QCD_OK;
+}
+
+qcd_status qcd_profile_end(qcd_profile *out)
+{
+    if (!out) return fail(QCD_ERR_INVALID_ARG, "profile_end: NULL argument");
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof_on) return fail(QCD_ERR_INVALID_ARG, "profile_end: no profiling window is open");
+    g_prof_on = false;
+    memset(out, 0, sizeof(*out));
+    qcd_status st = QCD_OK;
+    for (const ProfRec &r : g_prof) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(r.e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.e0, r.e1);
+        if (e != cudaSuccess && st == QCD_OK) st = check_cuda(e, "profile_end");
+        qcd_profile_entry &p = out->prec[r.prec];
+        p.launches += 1;
+        p.ms += ms;
+        p.bytes += r.bytes;
+        p.flops += r.flops;
+        p.sites += r.sites;
+        g_event_pool.push_back(r.e0);
+        g_event_pool.push_back(r.e1);
+    }
+    g_prof.clear();
+    return st;
+}
 
 qcd_status qcd_stream_sync(void *stream)
 {
@@ -328,6 +429,11 @@ void qcd_lattice_destroy(qcd_lattice *lat)
     cudaFree(lat->state);
     if (lat->state_host) cudaFreeHost(lat->state_host);
     for (auto &kv : lat->ws) cudaFree(kv.second.first);
+    for (auto &kv : lat->graphs) {
+        cudaGraphExecDestroy(kv.second.exec);
+        cudaGraphDestroy(kv.second.graph);
+    }
+    if (lat->capture_stream) cudaStreamDestroy(lat->capture_stream);
     delete lat;
 }
 

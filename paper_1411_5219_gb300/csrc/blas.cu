@@ -130,6 +130,24 @@ __global__ void cg_state_init_kernel(CgState *s, double tol2, double delta2, int
     s->maxiter = maxiter;
     s->status = CG_RUNNING;
     s->reliable_updates = 0;
+    s->trips = 0;
+    s->trip_limit = maxiter + 64;
+}
+
+// Graph control: run the reliable-update body when the iteration asked for it.
+__global__ void cg_ctrl_reliable_kernel(const CgState *st, cudaGraphConditionalHandle h)
+{
+    const int s = st->status;
+    cudaGraphSetConditional(h, (s == CG_RELIABLE || s == CG_CONVERGED) ? 1u : 0u);
+}
+
+// Graph control: repeat the loop body while CG runs; the trip cap bounds the
+// loop whatever the state holds.
+__global__ void cg_ctrl_loop_kernel(CgState *st, cudaGraphConditionalHandle h)
+{
+    st->trips += 1;
+    const bool go = st->status == CG_RUNNING && st->iter < st->maxiter && st->trips < st->trip_limit;
+    cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
 // r = rhs, p = r (both in the CG precision), x = 0, xs = 0; |rhs|^2.
@@ -276,12 +294,14 @@ static dim3 grid_of(const FieldView &f) { return dim3(site_blocks(nsites(f))); }
 cudaError_t launch_convert(const FieldView &dst, const FieldView &src, cudaStream_t s)
 {
     QCD_SP_CASES(dst.prec, SO, QCD_SP_CASES(src.prec, SI, convert_kernel<SO, SI><<<grid_of(dst), kThreads, 0, s>>>(dst, src)));
+    note_launches();
     return cudaGetLastError();
 }
 
 cudaError_t launch_zero(const FieldView &f, cudaStream_t s)
 {
     QCD_SP_CASES(f.prec, SF, zero_kernel<SF><<<grid_of(f), kThreads, 0, s>>>(f));
+    note_launches();
     return cudaGetLastError();
 }
 
@@ -289,6 +309,7 @@ cudaError_t launch_twist(const FieldView &out, const FieldView &in, const double
 {
     if (out.prec != in.prec) return cudaErrorInvalidValue;
     QCD_SP_CASES(out.prec, SF, twist_kernel<SF><<<grid_of(out), kThreads, 0, s>>>(out, in, c[0][0], c[0][1], c[1][0], c[1][1]));
+    note_launches();
     return cudaGetLastError();
 }
 
@@ -296,6 +317,7 @@ cudaError_t launch_norm2(const FieldView &f, const Reduction &red, FinalizeKind 
                          cudaStream_t s)
 {
     QCD_SP_CASES(f.prec, SF, norm2_kernel<SF><<<grid_of(f), kThreads, 0, s>>>(f, red, fin, stt, out));
+    note_launches();
     return cudaGetLastError();
 }
 
@@ -303,12 +325,28 @@ cudaError_t launch_diff_norm2(const FieldView &a, const FieldView &b, const Redu
 {
     if (a.prec != QCD_PREC_F64 || b.prec != QCD_PREC_F64) return cudaErrorInvalidValue;
     diff_norm2_kernel<<<grid_of(a), kThreads, 0, s>>>(a, b, red, out);
+    note_launches();
     return cudaGetLastError();
 }
 
 cudaError_t launch_cg_state_init(CgState *stt, double tol2, double delta2, int maxiter, cudaStream_t s)
 {
     cg_state_init_kernel<<<1, 1, 0, s>>>(stt, tol2, delta2, maxiter);
+    note_launches();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_ctrl_reliable(const CgState *stt, cudaGraphConditionalHandle h, cudaStream_t s)
+{
+    cg_ctrl_reliable_kernel<<<1, 1, 0, s>>>(stt, h);
+    note_launches();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_ctrl_loop(CgState *stt, cudaGraphConditionalHandle h, cudaStream_t s)
+{
+    cg_ctrl_loop_kernel<<<1, 1, 0, s>>>(stt, h);
+    note_launches();
     return cudaGetLastError();
 }
 
@@ -325,6 +363,7 @@ cudaError_t launch_cg_setup(const FieldView &rhs, const FieldView &r, const Fiel
     } else {
         return cudaErrorInvalidValue;
     }
+    note_launches();
     return cudaGetLastError();
 }
 
@@ -338,18 +377,21 @@ cudaError_t launch_cg_xr(const FieldView &x, const FieldView &p, const FieldView
     } else {
         return cudaErrorInvalidValue;
     }
+    note_launches();
     return cudaGetLastError();
 }
 
 cudaError_t launch_cg_p(const FieldView &p, const FieldView &r, CgState *stt, cudaStream_t s)
 {
     QCD_SP_CASES(p.prec, SF, cg_p_kernel<SF><<<grid_of(p), kThreads, 0, s>>>(p, r, stt));
+    note_launches();
     return cudaGetLastError();
 }
 
 cudaError_t launch_cg_accum_x(const FieldView &xhi, const FieldView &xs, cudaStream_t s)
 {
     QCD_SP_CASES(xs.prec, SS, cg_accum_x_kernel<SS><<<grid_of(xhi), kThreads, 0, s>>>(xhi, xs));
+    note_launches();
     return cudaGetLastError();
 }
 
@@ -362,6 +404,7 @@ cudaError_t launch_cg_true_residual(const FieldView &rhs, const FieldView &q, co
         QCD_SP_CASES(rs->prec, SS,
                      cg_true_residual_kernel<SS><<<grid_of(rhs), kThreads, 0, s>>>(rhs, q, rhi, *rs, true, red, stt));
     }
+    note_launches();
     return cudaGetLastError();
 }
 

@@ -166,6 +166,7 @@ cudaError_t launch_gauge_pack(const GaugeView &dst, int prec, int recon, const d
 {
     const int n = 2 * g.h;
     QCD_G_CASES(prec, recon, GF, gauge_pack_kernel<GF><<<(n + 127) / 128, 128, 0, s>>>(dst, aos, g));
+    note_launches();
     return cudaGetLastError();
 }
 
@@ -175,6 +176,7 @@ cudaError_t launch_gauge_convert(const GaugeView &dst, int dprec, int drecon, co
     const dim3 grid((g.h + 127) / 128, 8);
     QCD_G_CASES(dprec, drecon, GO,
                 QCD_G_CASES(sprec, srecon, GI, gauge_convert_kernel<GO, GI><<<grid, 128, 0, s>>>(dst, src, g.h)));
+    note_launches();
     return cudaGetLastError();
 }
 
@@ -182,6 +184,7 @@ cudaError_t launch_spinor_pack(const FieldView &dst, int parity, const double2 *
 {
     const int n = parity == 2 ? 2 * g.h : g.h;
     QCD_SP_CASES2(dst.prec, SF, spinor_pack_kernel<SF><<<(n + 127) / 128, 128, 0, s>>>(dst, parity, aos, g));
+    note_launches();
     return cudaGetLastError();
 }
 
@@ -189,6 +192,7 @@ cudaError_t launch_spinor_unpack(double2 *aos, const FieldView &src, int parity,
 {
     const int n = parity == 2 ? 2 * g.h : g.h;
     QCD_SP_CASES2(src.prec, SF, spinor_unpack_kernel<SF><<<(n + 127) / 128, 128, 0, s>>>(aos, src, parity, g));
+    note_launches();
     return cudaGetLastError();
 }
 

@@ -23,6 +23,16 @@ struct qcd_lattice {
     qcd::CgState *state_host = nullptr;  // pinned mirror
     // Named workspace buffers (staging, solver fields), grown on demand.
     mutable std::map<std::string, std::pair<void *, size_t>> ws;
+    // Instantiated CG-loop graphs keyed by solver configuration and field
+    // addresses, and the stream used only to capture them.
+    struct GraphEntry {
+        cudaGraph_t graph;
+        cudaGraphExec_t exec;
+        unsigned long long last_use;
+    };
+    mutable std::map<std::string, GraphEntry> graphs;
+    mutable unsigned long long graph_clock = 0;
+    mutable cudaStream_t capture_stream = nullptr;
 };
 
 struct qcd_gauge {
@@ -46,6 +56,10 @@ struct qcd_spinor {
 };
 
 namespace qcd {
+
+// True inside a qcd_profile_begin/end window (per-launch events cannot be
+// captured into conditional graph bodies, so the solver runs eagerly then).
+bool profiling_active();
 
 // Per-thread error message for qcd_last_error().
 qcd_status fail(qcd_status code, const char *fmt, ...);

@@ -482,6 +482,7 @@ struct CgState {
     int iter, maxiter;
     int status;
     int reliable_updates;
+    int trips, trip_limit;  // device-driven loop: body executions and their cap
     unsigned counter[4];
 };
 

@@ -5,6 +5,9 @@
 
 namespace qcd {
 
+// Counts kernel launches (qcd_kernel_launches).
+void note_launches(int n = 1);
+
 // A spinor field made of one (half) or two (full: even, odd) half fields of
 // h sites each, in storage precision `prec`.
 struct FieldView {
@@ -43,6 +46,10 @@ cudaError_t launch_cg_accum_x(const FieldView &xhi, const FieldView &xs, cudaStr
 // rhi = rhs - q (F64), |rhi|^2 -> reliable-update decision; rs = cast(rhi) if given.
 cudaError_t launch_cg_true_residual(const FieldView &rhs, const FieldView &q, const FieldView &rhi,
                                    const FieldView *rs, const Reduction &red, CgState *st, cudaStream_t s);
+
+// Graph control kernels (cudaGraphSetConditional on the loop / reliable-update handles).
+cudaError_t launch_cg_ctrl_reliable(const CgState *st, cudaGraphConditionalHandle h, cudaStream_t s);
+cudaError_t launch_cg_ctrl_loop(CgState *st, cudaGraphConditionalHandle h, cudaStream_t s);
 
 // Layout conversion between the host AoS form (FP64, lexicographic) and the
 // device SoA form.

@@ -22,6 +22,8 @@
 #include <chrono>
 #include <cmath>
 #include <algorithm>
+#include <cstdio>
+#include <vector>
 
 #include "qcd_handles.h"
 
@@ -122,6 +124,181 @@ cudaError_t apply_full_m(const OpCtx &c, const GaugeView &U, int recon, const Fi
     h.cy = coef_twist(dagger ? -c.a : c.a);
     h.cd = coef_real(-c.kappa);
     return hop(c.lat, U, recon, h, st);
+}
+
+
+// Everything one CG loop needs: operator context, gauge views, the FP64 and
+// inner fields, the reduction scratch and the device state.
+struct CgFields {
+    OpCtx c;
+    GaugeView Uh, Us;
+    int rh_recon, rs_recon;
+    bool mixed;
+    FieldView rhs, xh, rh, qh, th, sh;  // FP64
+    FieldView rs, ps, qs, ts, ss, xs;   // inner (aliases of the FP64 ones when not mixed)
+    Reduction red;
+    CgState *state;
+};
+
+// One CG iteration: q = A p (|Mhat p|^2 -> alpha), x += alpha p, r -= alpha q
+// (|r|^2 -> beta and status), p = r + beta p.  All return at once unless
+// the state is RUNNING.
+cudaError_t enqueue_iteration(const CgFields &f, cudaStream_t s)
+{
+    cudaError_t e = apply_normal(f.c, f.Us, f.rs_recon, f.ps, f.qs, f.ts, f.ss, true, true, s);
+    if (e == cudaSuccess) e = launch_cg_xr(f.mixed ? f.xs : f.xh, f.ps, f.rs, f.qs, f.red, f.state, s);
+    if (e == cudaSuccess) e = launch_cg_p(f.ps, f.rs, f.state, s);
+    return e;
+}
+
+// Reliable update / convergence check: x += xs (mixed), r = rhs - A x in
+// FP64 (|r|^2 -> DONE or RUNNING with beta = |r|^2 / |r_prev|^2), r_inner =
+// cast(r), then p = r + beta p.
+cudaError_t enqueue_true_residual(const CgFields &f, cudaStream_t s)
+{
+    cudaError_t e = cudaSuccess;
+    if (f.mixed) e = launch_cg_accum_x(f.xh, f.xs, s);
+    if (e == cudaSuccess) e = apply_normal(f.c, f.Uh, f.rh_recon, f.xh, f.qh, f.th, f.sh, false, false, s);
+    if (e == cudaSuccess) e = launch_cg_true_residual(f.rhs, f.qh, f.rh, f.mixed ? &f.rs : nullptr, f.red, f.state, s);
+    if (e == cudaSuccess) e = launch_cg_p(f.ps, f.rs, f.state, s);
+    return e;
+}
+
+cudaError_t read_state(const qcd_lattice *lat, cudaStream_t s)
+{
+    cudaError_t e = cudaMemcpyAsync(lat->state_host, lat->state, sizeof(CgState), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e;
+}
+
+// Host-driven loop: batches of iterations, the state read back after each.
+// The batch is sized from the observed convergence rate to end near the
+// next reliable update (mixed) or the target residual.
+cudaError_t cg_eager(const qcd_lattice *lat, const CgFields &f, cudaStream_t s)
+{
+    cudaError_t e = read_state(lat, s);
+    if (e != cudaSuccess) return e;
+    int batch = 2;
+    double last_rr = lat->state_host->rr;
+    int last_iter = 0;
+    for (;;) {
+        const int status = lat->state_host->status;
+        if (status == CG_DONE || status == CG_BREAKDOWN || status == CG_MAXITER) return cudaSuccess;
+        if (status == CG_CONVERGED || status == CG_RELIABLE)
+            if ((e = enqueue_true_residual(f, s)) != cudaSuccess) return e;
+        for (int k = 0; k < batch; ++k)
+            if ((e = enqueue_iteration(f, s)) != cudaSuccess) return e;
+        if ((e = read_state(lat, s)) != cudaSuccess) return e;
+        const CgState &hs = *lat->state_host;
+        const int done = hs.iter - last_iter;
+        if (done > 0 && hs.rr > 0.0 && last_rr > hs.rr && hs.status == CG_RUNNING) {
+            const double rate = std::log(last_rr / hs.rr) / done;
+            double rem = std::log(hs.rr / hs.rr_stop) / rate;
+            if (hs.delta2 > 0.0) rem = std::min(rem, std::log(hs.rr / (hs.delta2 * hs.rr_max)) / rate);
+            batch = (int)std::min(64.0, std::max(1.0, std::ceil(rem)));
+        } else {
+            batch = std::max(1, std::min(8, batch));
+        }
+        last_rr = hs.rr;
+        last_iter = hs.iter;
+    }
+}
+
+// The CG loop as one CUDA graph: a WHILE node whose body runs one iteration,
+// then an IF node that runs the reliable update when the iteration asked
+// for it, then a control kernel that keeps the loop going while the state
+// is RUNNING (bounded by iter < maxiter and a trip cap).  Built once per
+// configuration and field addresses and cached on the lattice.
+qcd_status cg_graph(const qcd_lattice *lat, const CgFields &f, cudaGraphExec_t *out)
+{
+    char key[512];
+    snprintf(key, sizeof(key), "%d|%a|%a|%d|%d|%d|%p|%p|%p|%p|%p|%p|%p|%p|%p|%p|%p|%p|%p|%p|%d|%d", (int)f.c.eo,
+             f.c.kappa, f.c.a, (int)f.mixed, f.rh_recon, f.rs_recon, f.Uh.data, f.Us.data, f.rhs.hv[0].data,
+             f.xh.hv[0].data, f.xh.hv[1].data, f.rh.hv[0].data, f.qh.hv[0].data, f.th.hv[0].data, f.sh.hv[0].data,
+             f.rs.hv[0].data, f.ps.hv[0].data, f.qs.hv[0].data, f.ts.hv[0].data, f.ss.hv[0].data, f.xs.hv[0].data,
+             (void *)f.state, f.rs.prec, f.rhs.nh);
+    auto it = lat->graphs.find(key);
+    if (it != lat->graphs.end()) {
+        it->second.last_use = ++lat->graph_clock;
+        *out = it->second.exec;
+        return QCD_OK;
+    }
+    if (!lat->capture_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&lat->capture_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return check_cuda(e, "solve_cg: capture stream");
+    }
+    cudaStream_t cs = lat->capture_stream;
+    cudaGraph_t g = nullptr, tmp = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphConditionalHandle hloop, hrel;
+    cudaGraphNode_t wnode, inode;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    cudaStreamCaptureStatus cst;
+    std::vector<cudaGraphNode_t> tail;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+#define G_TRY(x)                    \
+    if (e == cudaSuccess) e = (x);
+    G_TRY(cudaGraphConditionalHandleCreate(&hloop, g, 1, cudaGraphCondAssignDefault));
+    G_TRY(cudaGraphConditionalHandleCreate(&hrel, g, 0, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams wp{};
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = hloop;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    G_TRY(cudaGraphAddNode(&wnode, g, nullptr, nullptr, 0, &wp));
+    cudaGraph_t body = e == cudaSuccess ? wp.conditional.phGraph_out[0] : nullptr;
+    // body: one iteration, then the reliable-update decision
+    G_TRY(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    if (e == cudaSuccess) {
+        cudaError_t ec = enqueue_iteration(f, cs);
+        if (ec == cudaSuccess) ec = launch_cg_ctrl_reliable(f.state, hrel, cs);
+        if (ec == cudaSuccess) ec = cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &ndeps);
+        if (ec == cudaSuccess) tail.assign(deps, deps + ndeps);
+        cudaError_t ee = cudaStreamEndCapture(cs, &tmp);
+        e = ec != cudaSuccess ? ec : ee;
+    }
+    cudaGraphNodeParams ip{};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = hrel;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    G_TRY(cudaGraphAddNode(&inode, body, tail.data(), nullptr, tail.size(), &ip));
+    if (e == cudaSuccess) {
+        cudaGraph_t ibody = ip.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(cs, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t ec = enqueue_true_residual(f, cs);
+            cudaError_t ee = cudaStreamEndCapture(cs, &tmp);
+            e = ec != cudaSuccess ? ec : ee;
+        }
+    }
+    // after the IF node: the loop condition
+    G_TRY(cudaStreamBeginCaptureToGraph(cs, body, &inode, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+    if (e == cudaSuccess) {
+        cudaError_t ec = launch_cg_ctrl_loop(f.state, hloop, cs);
+        cudaError_t ee = cudaStreamEndCapture(cs, &tmp);
+        e = ec != cudaSuccess ? ec : ee;
+    }
+    G_TRY(cudaGraphInstantiate(&exec, g, 0));
+#undef G_TRY
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return check_cuda(e, "solve_cg: graph build");
+    }
+    // keep at most 16 graphs per lattice
+    if (lat->graphs.size() >= 16) {
+        auto old = lat->graphs.begin();
+        for (auto i = lat->graphs.begin(); i != lat->graphs.end(); ++i)
+            if (i->second.last_use < old->second.last_use) old = i;
+        cudaGraphExecDestroy(old->second.exec);
+        cudaGraphDestroy(old->second.graph);
+        lat->graphs.erase(old);
+    }
+    lat->graphs[key] = qcd_lattice::GraphEntry{g, exec, ++lat->graph_clock};
+    *out = exec;
+    return QCD_OK;
 }
 
 }  // namespace
@@ -244,62 +421,33 @@ extern "C" qcd_status qcd_solve_cg(const qcd_gauge *g, qcd_spinor *x, const qcd_
     }
 
     // ---- CG
-    const Reduction red = reduction_of(lat);
+    CgFields F{c, Uh, Us, g->recon, srecon, mixed, rhs, xh, rh, qh, th, sh, rs, ps, qs, ts, ss, xs,
+               reduction_of(lat), lat->state};
     const double delta = mixed ? prm->reliable_delta : 0.0;
     QCD_TRY(launch_cg_state_init(lat->state, prm->tol * prm->tol, delta * delta, prm->maxiter, s), "solve_cg: init");
-    QCD_TRY(launch_cg_setup(rhs, rs, ps, xh, mixed ? &xs : nullptr, red, lat->state, s), "solve_cg: setup");
+    QCD_TRY(launch_cg_setup(rhs, rs, ps, xh, mixed ? &xs : nullptr, F.red, lat->state, s), "solve_cg: setup");
 
-    auto read_state = [&]() -> cudaError_t {
-        cudaError_t e = cudaMemcpyAsync(lat->state_host, lat->state, sizeof(CgState), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        return e;
-    };
-    auto true_residual = [&]() -> cudaError_t {
-        cudaError_t e = cudaSuccess;
-        if (mixed) e = launch_cg_accum_x(xh, xs, s);
-        if (e == cudaSuccess) e = apply_normal(c, Uh, g->recon, xh, qh, th, sh, false, false, s);
-        if (e == cudaSuccess) e = launch_cg_true_residual(rhs, qh, rh, mixed ? &rs : nullptr, red, lat->state, s);
-        if (e == cudaSuccess) e = launch_cg_p(ps, rs, lat->state, s);
-        return e;
-    };
-
-    QCD_TRY(read_state(), "solve_cg: state");
-    int batch = 2;
-    double last_rr = lat->state_host->rr;
-    int last_iter = 0;
     qcd_status result = QCD_OK;
-    for (;;) {
+    const bool use_graph = !profiling_active();
+    if (use_graph) {
+        cudaGraphExec_t exec = nullptr;
+        qcd_status gst = cg_graph(lat, F, &exec);
+        if (gst != QCD_OK) return gst;
+        QCD_TRY(cudaGraphLaunch(exec, s), "solve_cg: graph launch");
+        QCD_TRY(read_state(lat, s), "solve_cg: state");
+        // kernels the graph ran: per trip the iteration and two control
+        // kernels, per reliable update its body
+        const int op = c.eo ? 4 : 2;
+        note_launches(lat->state_host->trips * (op + 4) + lat->state_host->reliable_updates * (op + 2 + (mixed ? 1 : 0)));
+    } else {
+        QCD_TRY(cg_eager(lat, F, s), "solve_cg: iterations");
+    }
+    {
         const int status = lat->state_host->status;
-        if (status == CG_DONE) break;
-        if (status == CG_BREAKDOWN) {
+        if (status == CG_BREAKDOWN)
             result = fail(QCD_ERR_BREAKDOWN, "solve_cg: breakdown (non-positive <p,Ap> or non-finite values)");
-            break;
-        }
-        if (status == CG_MAXITER) {
+        else if (status != CG_DONE)
             result = fail(QCD_ERR_NOT_CONVERGED, "solve_cg: maxiter reached");
-            break;
-        }
-        if (status == CG_CONVERGED || status == CG_RELIABLE) {
-            QCD_TRY(true_residual(), "solve_cg: true residual");
-        }
-        for (int k = 0; k < batch; ++k) {
-            QCD_TRY(apply_normal(c, Us, srecon, ps, qs, ts, ss, true, true, s), "solve_cg: operator");
-            QCD_TRY(launch_cg_xr(mixed ? xs : xh, ps, rs, qs, red, lat->state, s), "solve_cg: update");
-            QCD_TRY(launch_cg_p(ps, rs, lat->state, s), "solve_cg: update");
-        }
-        QCD_TRY(read_state(), "solve_cg: state");
-        // Size the next batch from the observed convergence rate.
-        const CgState &hs = *lat->state_host;
-        const int done = hs.iter - last_iter;
-        if (done > 0 && hs.rr > 0.0 && last_rr > hs.rr && hs.status == CG_RUNNING) {
-            const double rate = std::log(last_rr / hs.rr) / done;
-            const double rem = std::log(hs.rr / hs.rr_stop) / rate;
-            batch = (int)std::min(64.0, std::max(2.0, 0.9 * rem));
-        } else {
-            batch = std::min(64, batch * 2);
-        }
-        last_rr = hs.rr;
-        last_iter = hs.iter;
     }
     if (mixed && result != QCD_OK) QCD_TRY(launch_cg_accum_x(xh, xs, s), "solve_cg: accumulate");
 
@@ -321,7 +469,7 @@ extern "C" qcd_status qcd_solve_cg(const qcd_gauge *g, qcd_spinor *x, const qcd_
     }
     if (hs.status != CG_DONE) {  // true residual of the CG system, for the stats
         QCD_TRY(apply_normal(c, Uh, g->recon, xh, qh, th, sh, false, false, s), "solve_cg: residual");
-        QCD_TRY(launch_diff_norm2(qh, rhs, red, lat->red_out, s), "solve_cg: residual");
+        QCD_TRY(launch_diff_norm2(qh, rhs, F.red, lat->red_out, s), "solve_cg: residual");
         double r2[2];
         QCD_TRY(cudaMemcpyAsync(r2, lat->red_out, sizeof(r2), cudaMemcpyDeviceToHost, s), "solve_cg: residual");
         QCD_TRY(cudaStreamSynchronize(s), "solve_cg: residual");
@@ -339,7 +487,7 @@ extern "C" qcd_status qcd_solve_cg(const qcd_gauge *g, qcd_spinor *x, const qcd_
         QCD_TRY(apply_full_m(c, Uh, g->recon, mx, mx2, 1, s), "solve_cg: residual");
         chk = &mx2;
     }
-    QCD_TRY(launch_diff_norm2(*chk, bf, red, lat->red_out, s), "solve_cg: residual");
+    QCD_TRY(launch_diff_norm2(*chk, bf, F.red, lat->red_out, s), "solve_cg: residual");
     double r2[2];
     QCD_TRY(cudaMemcpyAsync(r2, lat->red_out, sizeof(r2), cudaMemcpyDeviceToHost, s), "solve_cg: residual");
     QCD_TRY(cudaStreamSynchronize(s), "solve_cg: residual");

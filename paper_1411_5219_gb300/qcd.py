@@ -38,6 +38,14 @@ class SolverStats(ctypes.Structure):
                 ("full_rel_residual", _d), ("seconds", _d)]
 
 
+class ProfileEntry(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong), ("ms", _d), ("bytes", _d), ("flops", _d), ("sites", _d)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("prec", ProfileEntry * 4)]
+
+
 # name -> (restype, argtypes); mirrors include/qcd.h
 _SIGS = {
     "qcd_status_string": (ctypes.c_char_p, [_i]),
@@ -62,6 +70,9 @@ _SIGS = {
     "qcd_apply_dslash": (_i, [_p, _p, _p, _i, _p]),
     "qcd_apply_M": (_i, [_p, _p, _p, _d, _d, _i, _i, _p]),
     "qcd_solve_cg": (_i, [_p, _p, _p, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats), _p]),
+    "qcd_profile_begin": (_i, []),
+    "qcd_profile_end": (_i, [ctypes.POINTER(Profile)]),
+    "qcd_kernel_launches": (ctypes.c_ulonglong, []),
 }
 
 _lib = None
@@ -278,3 +289,21 @@ def solve_cg(gauge: Gauge, x: Spinor, b: Spinor, kappa: float, mu: float = 0.0, 
         _check(status, "qcd_solve_cg")
     stats = {k: getattr(st, k) for k, _ in SolverStats._fields_}
     return status, stats
+
+
+def profile_begin():
+    """Start recording every hopping-kernel launch (qcd_profile_begin)."""
+    _check(lib().qcd_profile_begin(), "qcd_profile_begin")
+
+
+def profile_end():
+    """Stop recording; returns {prec: {launches, ms, bytes, flops, sites}}."""
+    pr = Profile()
+    _check(lib().qcd_profile_end(ctypes.byref(pr)), "qcd_profile_end")
+    inv = {v: k for k, v in PREC.items()}
+    return {inv[i]: {k: getattr(pr.prec[i], k) for k, _ in ProfileEntry._fields_} for i in range(4)}
+
+
+def kernel_launches() -> int:
+    """Kernels libqcd has launched since it was loaded."""
+    return int(lib().qcd_kernel_launches())

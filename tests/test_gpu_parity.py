@@ -345,3 +345,46 @@ def test_solve_eo_24x8_true_residual(q):
     xg = x.download()
     assert abs(F.rel_err(oracle.apply_m(U, xg, w["kappa"]), b) - st["full_rel_residual"]) <= 1e-12
     assert schur_residual_oracle(U, b, xg, w["kappa"], 0.0) <= 1.5e-10
+
+
+# ------------------------------------------- graph path, eager path, profiling
+
+@pytest.mark.parametrize("inner", ["f64", "f16"])
+def test_graph_and_eager_solves_bitwise_identical(q, inner):
+    """The solver replays a captured CUDA graph of the CG loop; inside a
+    profiling window it launches kernel by kernel.  Both run the same kernels
+    on the same data with fixed-order reductions: identical bits."""
+    dims = (8, 8, 8, 4)
+    lat, U, g = gauge(q, dims, eps=0.2, seed=77)
+    b = syn.gaussian_spinor(dims, 79)
+    bs = q.Spinor(lat, "full", "f64")
+    bs.upload(b)
+    outs = []
+    for mode in ("graph", "graph", "eager"):
+        x = q.Spinor(lat, "full", "f64")
+        if mode == "eager":
+            q.profile_begin()
+        status, st = q.solve_cg(g, x, bs, 0.16, 0.01, tol=1e-10, inner_prec=inner)
+        if mode == "eager":
+            prof = q.profile_end()
+            assert prof["f64"]["launches"] > 0
+        assert status == 0
+        outs.append((x.download(), st["iterations"], st["reliable_updates"]))
+    for o in outs[1:]:
+        assert np.array_equal(o[0], outs[0][0]) and o[1:] == outs[0][1:]
+
+
+def test_profile_accounting(q):
+    dims = (8, 6, 4, 10)
+    lat, U, g = gauge(q, dims)
+    h = syn.volume(dims) // 2
+    si, so = q.Spinor(lat, "odd", "f64"), q.Spinor(lat, "even", "f64")
+    q.profile_begin()
+    q.apply_dslash(g, so, si)
+    p = q.profile_end()
+    e = p["f64"]
+    assert e["launches"] == 1 and e["sites"] == h
+    assert e["bytes"] == h * (8 * 144 + 2 * 192) and e["flops"] == h * 1320 and e["ms"] > 0
+    n0 = q.kernel_launches()
+    q.apply_dslash(g, so, si)
+    assert q.kernel_launches() == n0 + 1
