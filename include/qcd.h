@@ -146,6 +146,24 @@ qcd_status qcd_spinor_convert(qcd_spinor *dst, const qcd_spinor *src, void *stre
 qcd_status qcd_spinor_norm2(const qcd_spinor *s, double *result_device, void *stream);
 void qcd_spinor_destroy(qcd_spinor *s);
 
+/* |x|^2 = sum_i x[i]^2 of n doubles at x_device (e.g. the planes of an F64
+ * spinor field), written to result_device (1 double), in FP64 with a fixed
+ * summation order -- the reduction of qcd_spinor_norm2 without any
+ * allocation.  The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory (a host framework that has
+ * reserved all device memory for its own allocator, or a latency-critical
+ * path that cannot accept cudaMalloc's implicit device synchronisation).
+ * It needs no lattice or spinor handle and calls no cudaMalloc or cudaFree:
+ * its scratch (8192 partial sums and a ticket counter, 64 KiB) is a static
+ * device array that every GPU loading the library holds until exit, which
+ * limits n to 16,777,216 doubles; larger n returns INVALID_ARG.  The first
+ * call on a device looks up that array's device address (make it before
+ * any stream capture).  All calls on a device share the array: calls that
+ * overlap on the GPU (different streams, no ordering) race; each call
+ * clears the counter before it launches.  n = 0 writes 0.  Errors:
+ * INVALID_ARG (NULL pointers, n too large); CUDA. */
+qcd_status qcd_norm2_noalloc(const double *x_device, size_t n, double *result_device, void *stream);
+
 /* -------------------------------------------------------------- operators */
 
 /* out = D_hop in (dagger = 0) or D_hop^dagger in (dagger = 1): the Dslash

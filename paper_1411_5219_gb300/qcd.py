@@ -73,6 +73,7 @@ _SIGS = {
     "qcd_profile_begin": (_i, []),
     "qcd_profile_end": (_i, [ctypes.POINTER(Profile)]),
     "qcd_kernel_launches": (ctypes.c_ulonglong, []),
+    "qcd_norm2_noalloc": (_i, [_p, ctypes.c_size_t, _p, _p]),
 }
 
 _lib = None
@@ -307,3 +308,12 @@ def profile_end():
 def kernel_launches() -> int:
     """Kernels libqcd has launched since it was loaded."""
     return int(lib().qcd_kernel_launches())
+
+
+NORM2_NOALLOC_MAX = 16_777_216
+
+
+def norm2_noalloc(x_ptr: int, n: int, result_ptr: int, stream=None):
+    """qcd_norm2_noalloc on raw device pointers (no allocation in the library)."""
+    _check(lib().qcd_norm2_noalloc(_p(x_ptr), ctypes.c_size_t(n), _p(result_ptr), _stream(stream)),
+           "qcd_norm2_noalloc")
