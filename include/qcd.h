@@ -65,7 +65,15 @@ typedef int qcd_status;
 #define QCD_ERR_BREAKDOWN 5     /* CG breakdown: <p,Ap> <= 0 or non-finite values */
 #define QCD_ERR_TIMEOUT 6       /* reserved for bounded device waits */
 
-typedef enum { QCD_PREC_F64 = 0, QCD_PREC_F32 = 1, QCD_PREC_F16 = 2, QCD_PREC_BF16 = 3 } qcd_prec;
+/* Storage precision of a field.  F64/F32/F16/BF16 are IEEE formats (F16
+ * spinors carry an FP32 per-site scale).  DF64 ("double-float") stores each
+ * real as the unevaluated sum hi + lo of two FP32 numbers (8 bytes, ~48
+ * significant bits) and its kernels compute in pairs of FP32 numbers with
+ * error-free transformations: FP64-accurate to ~1e-14 at FP32 instruction
+ * rates, since GB300 runs FP32 58x faster than FP64.  The paper computes all
+ * in double precision (Sec. 4); DF64 is this library's way to do so on
+ * GB300 and is always labelled as such. */
+typedef enum { QCD_PREC_F64 = 0, QCD_PREC_F32 = 1, QCD_PREC_F16 = 2, QCD_PREC_BF16 = 3, QCD_PREC_DF64 = 4 } qcd_prec;
 /* Link storage: 18 reals (full matrix) or 12 (rows 0 and 1; row 2 is
  * rebuilt as conj(row0 x row1), exact for SU(3)). */
 typedef enum { QCD_RECON_18 = 18, QCD_RECON_12 = 12 } qcd_recon;
@@ -192,8 +200,9 @@ typedef struct {
     int maxiter;           /* CG iteration cap */
     int eo;                /* 1: even-odd Schur complement (solves M x = b) */
     int normal;            /* eo = 0 only: 1 solves M^dagger M x = b, 0 solves M x = b (CGNR) */
-    qcd_prec inner_prec;   /* F64: plain FP64 CG; F32/F16/BF16: mixed precision with FP64 reliable updates */
-    qcd_recon inner_recon; /* link storage of the inner (sloppy) operator */
+    qcd_prec inner_prec;   /* F64: plain FP64 CG; F32/F16/BF16/DF64: inner iterations in that precision with FP64
+                              reliable updates (DF64 accumulates its correction in DF64, the others in FP32) */
+    qcd_recon inner_recon; /* link storage of the inner (sloppy) operator (DF64 always uses 18) */
     double reliable_delta; /* mixed: reliable update when |r| < delta * max|r| since the last one (e.g. 0.1) */
 } qcd_solver_params;
 
@@ -244,7 +253,7 @@ typedef struct {
     double sites;  /* summed output sites */
 } qcd_profile_entry;
 typedef struct {
-    qcd_profile_entry prec[4];
+    qcd_profile_entry prec[5];
 } qcd_profile;
 qcd_status qcd_profile_begin(void);
 qcd_status qcd_profile_end(qcd_profile *out);

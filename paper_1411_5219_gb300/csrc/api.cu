@@ -45,7 +45,8 @@ static cudaEvent_t pool_event()
 static double spinor_site_bytes(int prec)
 {
     switch (prec) {
-    case QCD_PREC_F64: return 192;
+    case QCD_PREC_F64:
+    case QCD_PREC_DF64: return 192;
     case QCD_PREC_F32: return 96;
     case QCD_PREC_F16: return 52;
     default: return 48;
@@ -53,7 +54,7 @@ static double spinor_site_bytes(int prec)
 }
 static double link_bytes(int prec, int recon)
 {
-    const double w = prec == QCD_PREC_F64 ? 8 : prec == QCD_PREC_F32 ? 4 : 2;
+    const double w = (prec == QCD_PREC_F64 || prec == QCD_PREC_DF64) ? 8 : prec == QCD_PREC_F32 ? 4 : 2;
     return w * recon;
 }
 
@@ -79,19 +80,19 @@ qcd_status check_cuda(cudaError_t e, const char *what)
 
 // ----------------------------------------------------------------- sizes
 
-int spinor_planes(int prec) { return prec == QCD_PREC_F64 ? 12 : prec == QCD_PREC_F32 ? 6 : 3; }
+int spinor_planes(int prec) { return (prec == QCD_PREC_F64 || prec == QCD_PREC_DF64) ? 12 : prec == QCD_PREC_F32 ? 6 : 3; }
 size_t spinor_plane_elem_bytes(int) { return 16; }
 size_t spinor_half_bytes(int prec, int stride) { return (size_t)spinor_planes(prec) * 16 * stride; }
 size_t spinor_half_norm_bytes(int prec, int stride) { return prec == QCD_PREC_F16 ? (size_t)4 * stride : 0; }
 
 int gauge_planes(int prec, int recon)
 {
-    if (prec == QCD_PREC_F64) return recon / 2;
+    if (prec == QCD_PREC_F64 || prec == QCD_PREC_DF64) return recon / 2;
     return recon == 18 ? 9 : 3;
 }
 size_t gauge_plane_elem_bytes(int prec, int recon)
 {
-    if (prec == QCD_PREC_F64) return 16;
+    if (prec == QCD_PREC_F64 || prec == QCD_PREC_DF64) return 16;
     if (prec == QCD_PREC_F32) return recon == 18 ? 8 : 16;
     return recon == 18 ? 4 : 8;
 }
@@ -100,7 +101,7 @@ size_t gauge_bytes(int prec, int recon, int stride)
     return (size_t)8 * gauge_planes(prec, recon) * gauge_plane_elem_bytes(prec, recon) * stride;
 }
 
-static bool valid_prec(int p) { return p >= QCD_PREC_F64 && p <= QCD_PREC_BF16; }
+static bool valid_prec(int p) { return p >= QCD_PREC_F64 && p <= QCD_PREC_DF64; }
 static bool valid_recon(int r) { return r == 18 || r == 12; }
 
 // ----------------------------------------------------------------- views
@@ -231,6 +232,8 @@ cudaError_t launch_dslash_f64(int recon, const DslashLaunch &a, cudaStream_t s);
 cudaError_t launch_dslash_f32(int recon, const DslashLaunch &a, cudaStream_t s);
 cudaError_t launch_dslash_f16(int recon, const DslashLaunch &a, cudaStream_t s);
 cudaError_t launch_dslash_bf16(int recon, const DslashLaunch &a, cudaStream_t s);
+cudaError_t launch_dslash_df64_d0(int recon, const DslashLaunch &a, cudaStream_t s);
+cudaError_t launch_dslash_df64_d1(int recon, const DslashLaunch &a, cudaStream_t s);
 
 cudaError_t launch_dslash(int prec, int recon, const DslashLaunch &a, cudaStream_t s)
 {
@@ -239,6 +242,7 @@ cudaError_t launch_dslash(int prec, int recon, const DslashLaunch &a, cudaStream
     case QCD_PREC_F32: return launch_dslash_f32(recon, a, s);
     case QCD_PREC_F16: return launch_dslash_f16(recon, a, s);
     case QCD_PREC_BF16: return launch_dslash_bf16(recon, a, s);
+    case QCD_PREC_DF64: return a.dagger ? launch_dslash_df64_d1(recon, a, s) : launch_dslash_df64_d0(recon, a, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -269,7 +273,7 @@ cudaError_t hop(const qcd_lattice *lat, const GaugeView &U, int recon, const Hop
     if (h.plain)
         a.epi = EPI_PLAIN;
     else if (!h.y)
-        a.epi = h.twisted ? EPI_CPLX_D : EPI_REAL_D;
+        a.epi = EPI_CPLX_D;  // out = cd .* D in (real coefficients are the im = 0 case)
     else
         a.epi = h.twisted ? EPI_CPLX_YD : EPI_REAL_YD;
     a.reduce = h.reduce;
@@ -401,7 +405,8 @@ qcd_status qcd_lattice_create(const int dims[4], int t_bc, qcd_lattice **out)
     g.tbc = (double)t_bc;
     lat->h = (int)h;
     lat->stride = (int)((h + 63) / 64 * 64);
-    lat->red_cap = 2 * ((size_t)site_blocks((int)V) + 64);
+    // partials of the largest grid: 64-thread blocks over all V sites
+    lat->red_cap = 2 * (((size_t)V + 63) / 64 + 64);
     cudaError_t e = cudaMalloc(&lat->red_partials, lat->red_cap * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&lat->red_counter, 64);
     if (e == cudaSuccess) e = cudaMalloc(&lat->red_out, 8 * sizeof(double));

@@ -285,6 +285,10 @@ __global__ void __launch_bounds__(kThreads) cg_true_residual_kernel(const FieldV
         using SF = SpBF16;                             \
         __VA_ARGS__;                                   \
     } break;                                           \
+    case QCD_PREC_DF64: {                              \
+        using SF = SpDF64;                             \
+        __VA_ARGS__;                                   \
+    } break;                                           \
     default:                                           \
         return cudaErrorInvalidValue;                  \
     }
@@ -357,6 +361,8 @@ cudaError_t launch_cg_setup(const FieldView &rhs, const FieldView &r, const Fiel
     const bool has = xs != nullptr;
     if (x.prec == QCD_PREC_F64 && r.prec == QCD_PREC_F64 && !has) {
         cg_setup_kernel<SpF64, SpF64, SpF32><<<grid_of(rhs), kThreads, 0, s>>>(rhs, r, p, x, xsv, false, red, stt);
+    } else if (x.prec == QCD_PREC_F64 && has && xs->prec == QCD_PREC_DF64 && r.prec == QCD_PREC_DF64) {
+        cg_setup_kernel<SpDF64, SpF64, SpDF64><<<grid_of(rhs), kThreads, 0, s>>>(rhs, r, p, x, xsv, true, red, stt);
     } else if (x.prec == QCD_PREC_F64 && has && xs->prec == QCD_PREC_F32) {
         QCD_SP_CASES(r.prec, SR,
                      cg_setup_kernel<SR, SpF64, SpF32><<<grid_of(rhs), kThreads, 0, s>>>(rhs, r, p, x, xsv, true, red, stt));
@@ -372,6 +378,8 @@ cudaError_t launch_cg_xr(const FieldView &x, const FieldView &p, const FieldView
 {
     if (x.prec == QCD_PREC_F64 && p.prec == QCD_PREC_F64) {
         cg_xr_kernel<SpF64, SpF64><<<grid_of(x), kThreads, 0, s>>>(x, p, r, q, red, stt);
+    } else if (x.prec == QCD_PREC_DF64 && p.prec == QCD_PREC_DF64) {
+        cg_xr_kernel<SpDF64, SpDF64><<<grid_of(x), kThreads, 0, s>>>(x, p, r, q, red, stt);
     } else if (x.prec == QCD_PREC_F32) {
         QCD_SP_CASES(p.prec, SF, cg_xr_kernel<SpF32, SF><<<grid_of(x), kThreads, 0, s>>>(x, p, r, q, red, stt));
     } else {

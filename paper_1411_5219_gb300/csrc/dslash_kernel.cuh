@@ -48,8 +48,16 @@ __device__ __forceinline__ HalfSpinor<R> project(const Spinor<R> &p)
 
 // acc (+)= the full spinor rebuilt from the multiplied half spinor u:
 // upper = u, lower = -S B^dagger u.
-template <typename R, int MU, int S, bool kFirst>
-__device__ __forceinline__ void accumulate(Spinor<R> &acc, const HalfSpinor<R> &u)
+template <typename R>
+__device__ __forceinline__ cx<R> wadd(cx<R> acc, R w, cx<R> v)
+{
+    return {fma(w, v.re, acc.re), fma(w, v.im, acc.im)};
+}
+
+// kW: the hop carries a weight w (the FP16 per-site scale, with the
+// boundary sign), applied in the accumulating FMAs.
+template <typename R, int MU, int S, bool kFirst, bool kW>
+__device__ __forceinline__ void accumulate(Spinor<R> &acc, const HalfSpinor<R> &u, R w)
 {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -67,11 +75,21 @@ __device__ __forceinline__ void accumulate(Spinor<R> &acc, const HalfSpinor<R> &
             l2 = S > 0 ? -u.c[0][c] : u.c[0][c];
             l3 = S > 0 ? -u.c[1][c] : u.c[1][c];
         }
-        if (kFirst) {
+        if (kFirst && kW) {
+            acc.c[0][c] = w * u.c[0][c];
+            acc.c[1][c] = w * u.c[1][c];
+            acc.c[2][c] = w * l2;
+            acc.c[3][c] = w * l3;
+        } else if (kFirst) {
             acc.c[0][c] = u.c[0][c];
             acc.c[1][c] = u.c[1][c];
             acc.c[2][c] = l2;
             acc.c[3][c] = l3;
+        } else if (kW) {
+            acc.c[0][c] = wadd(acc.c[0][c], w, u.c[0][c]);
+            acc.c[1][c] = wadd(acc.c[1][c], w, u.c[1][c]);
+            acc.c[2][c] = wadd(acc.c[2][c], w, l2);
+            acc.c[3][c] = wadd(acc.c[3][c], w, l3);
         } else {
             acc.c[0][c] = acc.c[0][c] + u.c[0][c];
             acc.c[1][c] = acc.c[1][c] + u.c[1][c];
@@ -114,29 +132,53 @@ __device__ __forceinline__ void negate(HalfSpinor<R> &h)
         for (int c = 0; c < 3; ++c) h.c[s][c] = -h.c[s][c];
 }
 
-// One hop: load the neighbour spinor and the link, project, multiply,
+// One hop from already fetched raw data: decode, project, multiply,
 // rebuild and accumulate.  `flip` applies the boundary factor -1.
 template <typename SF, typename GF, int MU, int S, bool kAdj, bool kFirst>
-__device__ __forceinline__ void hop(Spinor<typename SF::R> &acc, const SpinorView &in, const GaugeView &U, int nb,
-                                    int lblock, int lidx, bool flip)
+__device__ __forceinline__ void hop(Spinor<typename SF::R> &acc, const typename SF::Raw &rs,
+                                    const typename GF::Raw &ru, bool flip)
 {
     using R = typename SF::R;
-    const Spinor<R> psi = SF::load(in, nb);
-    const Link<R> u = GF::load(U, lblock, lidx);
-    HalfSpinor<R> h = project<R, MU, S>(psi);
+    const Spinor<R> psi = SF::decode(rs);
+    const Link<R> u = GF::decode(ru);
+    const HalfSpinor<R> h = project<R, MU, S>(psi);
     HalfSpinor<R> uh = su3_mul<R, kAdj>(u, h);
-    if (flip) negate(uh);
-    accumulate<R, MU, S, kFirst>(acc, uh);
+    if (SF::kScaled) {
+        const R w = flip ? -SF::scale(rs) : SF::scale(rs);
+        accumulate<R, MU, S, kFirst, true>(acc, uh, w);
+    } else {
+        if (flip) negate(uh);
+        accumulate<R, MU, S, kFirst, false>(acc, uh, R(1));
+    }
+}
+
+// Threads per block: FP64 kernels hold ~170 registers (2-3 blocks of 128
+// per SM), so they use blocks of 64 to spread the grid evenly over the 152
+// SMs; the FP32/16-bit kernels use 128.
+template <typename SF>
+__host__ __device__ constexpr int dslash_tpb()
+{
+    return sizeof(typename SF::R) == 8 ? 64 : 128;
+}
+
+// Blocks per SM the register budget must allow: six 64-thread FP64 blocks
+// (<= 170 registers) put a 24^3 x 8 half lattice (864 blocks) in a single
+// wave on 152 SMs.
+template <typename SF>
+__host__ __device__ constexpr int dslash_min_blocks()
+{
+    return sizeof(typename SF::R) == 8 ? 6 : 1;
 }
 
 template <typename SF, typename GF, int kDagger, int kEpi, bool kReduce>
-__global__ void __launch_bounds__(kThreads) dslash_kernel(const DslashLaunch a)
+__global__ void __launch_bounds__(dslash_tpb<SF>(), dslash_min_blocks<SF>()) dslash_kernel(const DslashLaunch a)
 {
     using R = typename SF::R;
     if (a.check_status && a.state->status != CG_RUNNING) return;
     constexpr int SF_ = kDagger ? -1 : +1;  // projector sign of forward hops
     constexpr int SB_ = -SF_;                // ... of backward hops
-    const int nbp = (a.g.h + kThreads - 1) / kThreads;
+    constexpr int TPB = dslash_tpb<SF>();
+    const int nbp = (a.g.h + TPB - 1) / TPB;
     const int p = a.both ? (int)(blockIdx.x >= (unsigned)nbp) : a.out_parity;
     const int i = (blockIdx.x - (a.both ? p * nbp : 0)) * blockDim.x + threadIdx.x;
     double red[1] = {0.0};
@@ -146,38 +188,60 @@ __global__ void __launch_bounds__(kThreads) dslash_kernel(const DslashLaunch a)
         const SiteCoords c = site_coords(g, i, p);
         const int base = i - c.xh;
         const int fwd = p * 4, bwd = (1 - p) * 4;
-        Spinor<R> acc;
-        // x
+        // neighbour half-site, link block and link index of the 8 hops in
+        // the order x+, x-, y+, y-, z+, z-, t+, t-
+        int nb[8], lb[8], li[8];
+        bool fl[8];
         {
             const int xf = c.x + 1 == g.L[0] ? 0 : c.x + 1;
             const int xb = c.x == 0 ? g.L[0] - 1 : c.x - 1;
-            const int nf = base + (xf >> 1), nbk = base + (xb >> 1);
-            hop<SF, GF, 0, SF_, false, true>(acc, in, a.U, nf, fwd + 0, i, false);
-            hop<SF, GF, 0, SB_, true, false>(acc, in, a.U, nbk, bwd + 0, nbk, false);
-        }
-        // y
-        {
-            const int nf = c.y == g.L[1] - 1 ? i - (g.L[1] - 1) * g.sy : i + g.sy;
-            const int nbk = c.y == 0 ? i + (g.L[1] - 1) * g.sy : i - g.sy;
-            hop<SF, GF, 1, SF_, false, false>(acc, in, a.U, nf, fwd + 1, i, false);
-            hop<SF, GF, 1, SB_, true, false>(acc, in, a.U, nbk, bwd + 1, nbk, false);
-        }
-        // z
-        {
-            const int nf = c.z == g.L[2] - 1 ? i - (g.L[2] - 1) * g.sz : i + g.sz;
-            const int nbk = c.z == 0 ? i + (g.L[2] - 1) * g.sz : i - g.sz;
-            hop<SF, GF, 2, SF_, false, false>(acc, in, a.U, nf, fwd + 2, i, false);
-            hop<SF, GF, 2, SB_, true, false>(acc, in, a.U, nbk, bwd + 2, nbk, false);
-        }
-        // t (boundary factor on the wrapping hop)
-        {
+            nb[0] = base + (xf >> 1);
+            nb[1] = base + (xb >> 1);
+            nb[2] = c.y == g.L[1] - 1 ? i - (g.L[1] - 1) * g.sy : i + g.sy;
+            nb[3] = c.y == 0 ? i + (g.L[1] - 1) * g.sy : i - g.sy;
+            nb[4] = c.z == g.L[2] - 1 ? i - (g.L[2] - 1) * g.sz : i + g.sz;
+            nb[5] = c.z == 0 ? i + (g.L[2] - 1) * g.sz : i - g.sz;
             const bool wf = c.t == g.L[3] - 1, wb = c.t == 0;
-            const int nf = wf ? i - (g.L[3] - 1) * g.st : i + g.st;
-            const int nbk = wb ? i + (g.L[3] - 1) * g.st : i - g.st;
+            nb[6] = wf ? i - (g.L[3] - 1) * g.st : i + g.st;
+            nb[7] = wb ? i + (g.L[3] - 1) * g.st : i - g.st;
             const bool anti = g.tbc < 0.0;
-            hop<SF, GF, 3, SF_, false, false>(acc, in, a.U, nf, fwd + 3, i, anti && wf);
-            hop<SF, GF, 3, SB_, true, false>(acc, in, a.U, nbk, bwd + 3, nbk, anti && wb);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                lb[k] = (k & 1 ? bwd : fwd) + (k >> 1);
+                li[k] = k & 1 ? nb[k] : i;
+                fl[k] = false;
+            }
+            fl[6] = anti && wf;
+            fl[7] = anti && wb;
         }
+        Spinor<R> acc;
+        // software pipeline: the loads of hop k+1 are issued before the
+        // arithmetic of hop k
+        typename SF::Raw rs = SF::fetch(in, nb[0]);
+        typename GF::Raw ru = GF::fetch(a.U, lb[0], li[0]);
+#define QCD_HOP(K, MU, S, ADJ, FIRST)                                        \
+    {                                                                      \
+        typename SF::Raw rs_n;                                             \
+        typename GF::Raw ru_n;                                             \
+        if (K < 7) {                                                       \
+            rs_n = SF::fetch(in, nb[(K + 1) & 7]);                         \
+            ru_n = GF::fetch(a.U, lb[(K + 1) & 7], li[(K + 1) & 7]);       \
+        }                                                                  \
+        hop<SF, GF, MU, S, ADJ, FIRST>(acc, rs, ru, fl[K]);                \
+        if (K < 7) {                                                       \
+            rs = rs_n;                                                     \
+            ru = ru_n;                                                     \
+        }                                                                  \
+    }
+        QCD_HOP(0, 0, SF_, false, true)
+        QCD_HOP(1, 0, SB_, true, false)
+        QCD_HOP(2, 1, SF_, false, false)
+        QCD_HOP(3, 1, SB_, true, false)
+        QCD_HOP(4, 2, SF_, false, false)
+        QCD_HOP(5, 2, SB_, true, false)
+        QCD_HOP(6, 3, SF_, false, false)
+        QCD_HOP(7, 3, SB_, true, false)
+#undef QCD_HOP
         // epilogue
         Spinor<R> out;
         if (kEpi == EPI_PLAIN) {
@@ -227,28 +291,33 @@ __global__ void __launch_bounds__(kThreads) dslash_kernel(const DslashLaunch a)
     if (kReduce) grid_reduce<1>(red, a.red, a.fin, a.state, a.red_out);
 }
 
-// Dispatch over dagger / epilogue / reduction for one format pair.
-template <typename SF, typename GF>
-cudaError_t launch_dslash_fmt(const DslashLaunch &a, cudaStream_t s)
+// Dispatch over epilogue / reduction for one format pair and one dagger
+// value.  (The real-scale epilogue without y has no caller and is not
+// instantiated.)
+template <typename SF, typename GF, int D>
+cudaError_t launch_dslash_dag(const DslashLaunch &a, cudaStream_t s)
 {
-    const dim3 grid(site_blocks(a.g.h) * (a.both ? 2 : 1)), block(kThreads);
-#define QCD_DSL(D, E, RD)                                                   \
-    if (a.dagger == D && a.epi == E && a.reduce == RD) {                    \
+    constexpr int TPB = dslash_tpb<SF>();
+    const dim3 grid((a.g.h + TPB - 1) / TPB * (a.both ? 2 : 1)), block(TPB);
+#define QCD_DSL(E, RD)                                                      \
+    if (a.epi == E && a.reduce == RD) {                                     \
         dslash_kernel<SF, GF, D, E, RD><<<grid, block, 0, s>>>(a);          \
         return cudaGetLastError();                                          \
     }
-#define QCD_DSL_E(D, E) QCD_DSL(D, E, false) QCD_DSL(D, E, true)
-#define QCD_DSL_D(D)                                                        \
-    QCD_DSL(D, EPI_PLAIN, false)                                            \
-    QCD_DSL(D, EPI_REAL_D, false)                                           \
-    QCD_DSL(D, EPI_CPLX_D, false)                                           \
-    QCD_DSL_E(D, EPI_REAL_YD) QCD_DSL_E(D, EPI_CPLX_YD)
-    QCD_DSL_D(0)
-    QCD_DSL_D(1)
-#undef QCD_DSL_D
-#undef QCD_DSL_E
+    QCD_DSL(EPI_PLAIN, false)
+    QCD_DSL(EPI_CPLX_D, false)
+    QCD_DSL(EPI_REAL_YD, false)
+    QCD_DSL(EPI_REAL_YD, true)
+    QCD_DSL(EPI_CPLX_YD, false)
+    QCD_DSL(EPI_CPLX_YD, true)
 #undef QCD_DSL
     return cudaErrorInvalidValue;
+}
+
+template <typename SF, typename GF>
+cudaError_t launch_dslash_fmt(const DslashLaunch &a, cudaStream_t s)
+{
+    return a.dagger ? launch_dslash_dag<SF, GF, 1>(a, s) : launch_dslash_dag<SF, GF, 0>(a, s);
 }
 
 }  // namespace qcd

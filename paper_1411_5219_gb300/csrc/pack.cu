@@ -135,6 +135,12 @@ __global__ void spinor_unpack_kernel(double2 *aos, const FieldView src, const in
     } else if (prec == QCD_PREC_BF16 && recon == 12) {                        \
         using GF = G16<__nv_bfloat16, 12>;                                    \
         __VA_ARGS__;                                                          \
+    } else if (prec == QCD_PREC_DF64 && recon == 18) {                        \
+        using GF = GDF64<18>;                                                 \
+        __VA_ARGS__;                                                          \
+    } else if (prec == QCD_PREC_DF64 && recon == 12) {                        \
+        using GF = GDF64<12>;                                                 \
+        __VA_ARGS__;                                                          \
     } else {                                                                  \
         return cudaErrorInvalidValue;                                         \
     }
@@ -155,6 +161,10 @@ __global__ void spinor_unpack_kernel(double2 *aos, const FieldView src, const in
     } break;                              \
     case QCD_PREC_BF16: {                 \
         using SF = SpBF16;                \
+        __VA_ARGS__;                      \
+    } break;                              \
+    case QCD_PREC_DF64: {                 \
+        using SF = SpDF64;                \
         __VA_ARGS__;                      \
     } break;                              \
     default:                              \

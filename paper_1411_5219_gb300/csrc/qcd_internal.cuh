@@ -21,6 +21,7 @@
 #include <stdint.h>
 
 #include "../../include/qcd.h"
+#include "df64.cuh"
 
 namespace qcd {
 
@@ -112,6 +113,26 @@ struct SpF64 {
     using R = double;
     static constexpr int kPlanes = 12;  // double2 per plane
     static constexpr size_t kBytesPerSite = 192;
+    static constexpr bool kScaled = false;
+    struct Raw {
+        double2 d[12];
+    };
+    __device__ __forceinline__ static Raw fetch(const SpinorView &v, int i)
+    {
+        Raw r;
+        const double2 *p = static_cast<const double2 *>(v.data) + i;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) r.d[k] = __ldg(p + (size_t)k * v.stride);
+        return r;
+    }
+    __device__ __forceinline__ static Spinor<R> decode(const Raw &r)
+    {
+        Spinor<R> s;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) s.c[k / 3][k % 3] = mk(r.d[k].x, r.d[k].y);
+        return s;
+    }
+    __device__ __forceinline__ static R scale(const Raw &) { return 1.0; }
     __device__ __forceinline__ static Spinor<R> load(const SpinorView &v, int i)
     {
         Spinor<R> s;
@@ -135,6 +156,29 @@ struct SpF32 {
     using R = float;
     static constexpr int kPlanes = 6;  // float4 (two complex) per plane
     static constexpr size_t kBytesPerSite = 96;
+    static constexpr bool kScaled = false;
+    struct Raw {
+        float4 d[6];
+    };
+    __device__ __forceinline__ static Raw fetch(const SpinorView &v, int i)
+    {
+        Raw r;
+        const float4 *p = static_cast<const float4 *>(v.data) + i;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) r.d[k] = __ldg(p + (size_t)k * v.stride);
+        return r;
+    }
+    __device__ __forceinline__ static Spinor<R> decode(const Raw &r)
+    {
+        Spinor<R> s;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            s.c[(2 * k) / 3][(2 * k) % 3] = mk(r.d[k].x, r.d[k].y);
+            s.c[(2 * k + 1) / 3][(2 * k + 1) % 3] = mk(r.d[k].z, r.d[k].w);
+        }
+        return s;
+    }
+    __device__ __forceinline__ static R scale(const Raw &) { return 1.0f; }
     __device__ __forceinline__ static Spinor<R> load(const SpinorView &v, int i)
     {
         Spinor<R> s;
@@ -187,12 +231,83 @@ struct Half16<__nv_bfloat16> {
     }
 };
 
+// Double-float spinor: twelve float4 planes, (hi.re, hi.im, lo.re, lo.im)
+// per complex component, 192 bytes per site like FP64.
+struct SpDF64 {
+    using R = df;
+    static constexpr int kPlanes = 12;
+    static constexpr size_t kBytesPerSite = 192;
+    static constexpr bool kScaled = false;
+    struct Raw {
+        float4 d[12];
+    };
+    __device__ __forceinline__ static Raw fetch(const SpinorView &v, int i)
+    {
+        Raw r;
+        const float4 *p = static_cast<const float4 *>(v.data) + i;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) r.d[k] = __ldg(p + (size_t)k * v.stride);
+        return r;
+    }
+    __device__ __forceinline__ static Spinor<R> decode(const Raw &r)
+    {
+        Spinor<R> s;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) s.c[k / 3][k % 3] = cx<R>{df(r.d[k].x, r.d[k].z), df(r.d[k].y, r.d[k].w)};
+        return s;
+    }
+    __device__ __forceinline__ static R scale(const Raw &) { return df(1.0f, 0.0f); }
+    __device__ __forceinline__ static Spinor<R> load(const SpinorView &v, int i) { return decode(fetch(v, i)); }
+    __device__ __forceinline__ static void store(const SpinorView &v, int i, const Spinor<R> &s)
+    {
+        float4 *p = static_cast<float4 *>(v.data) + i;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const cx<R> a = s.c[k / 3][k % 3];
+            p[(size_t)k * v.stride] = make_float4(a.re.hi, a.im.hi, a.re.lo, a.im.lo);
+        }
+    }
+};
+
 // 16-bit spinor: three uint4 planes (four complex each); FP16 adds a scale.
 template <typename H, bool kNorm>
 struct Sp16 {
     using R = float;
     static constexpr int kPlanes = 3;
     static constexpr size_t kBytesPerSite = 48 + (kNorm ? 4 : 0);
+    // decode() leaves the FP16 per-site scale out; scale() returns it, so the
+    // hopping kernel can fold it into its accumulation instead of scaling
+    // all 24 components.
+    static constexpr bool kScaled = kNorm;
+    struct Raw {
+        uint4 w[3];
+        float sc;
+    };
+    __device__ __forceinline__ static Raw fetch(const SpinorView &v, int i)
+    {
+        Raw r;
+        const uint4 *p = static_cast<const uint4 *>(v.data) + i;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) r.w[k] = __ldg(p + (size_t)k * v.stride);
+        r.sc = kNorm ? __ldg(v.norm + i) : 1.0f;
+        return r;
+    }
+    __device__ __forceinline__ static Spinor<R> decode(const Raw &r)
+    {
+        Spinor<R> s;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const uint32_t ws[4] = {r.w[k].x, r.w[k].y, r.w[k].z, r.w[k].w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float2 f = Half16<H>::to2(ws[j]);
+                const int c = 4 * k + j;
+                s.c[c / 3][c % 3] = mk(f.x, f.y);
+            }
+        }
+        return s;
+    }
+    __device__ __forceinline__ static R scale(const Raw &r) { return r.sc; }
     __device__ __forceinline__ static Spinor<R> load(const SpinorView &v, int i)
     {
         Spinor<R> s;
@@ -255,6 +370,25 @@ struct GF64 {
     static constexpr int kRecon_ = kRecon;
     static constexpr int kPlanes = kRecon / 2;  // double2 (one complex) per plane
     static constexpr size_t kBytesPerLink = kRecon * 8;
+    struct Raw {
+        double2 d[kPlanes];
+    };
+    __device__ __forceinline__ static Raw fetch(const GaugeView &g, int block, int i)
+    {
+        Raw r;
+        const double2 *p = static_cast<const double2 *>(g.data) + (size_t)block * kPlanes * g.stride + i;
+#pragma unroll
+        for (int k = 0; k < kPlanes; ++k) r.d[k] = __ldg(p + (size_t)k * g.stride);
+        return r;
+    }
+    __device__ __forceinline__ static Link<R> decode(const Raw &r)
+    {
+        Link<R> u;
+#pragma unroll
+        for (int k = 0; k < kPlanes; ++k) u.m[k / 3][k % 3] = mk(r.d[k].x, r.d[k].y);
+        reconstruct_row2<kRecon>(u);
+        return u;
+    }
     __device__ __forceinline__ static Link<R> load(const GaugeView &g, int block, int i)
     {
         Link<R> u;
@@ -282,6 +416,36 @@ struct GF32 {
     // recon-18: nine float2 planes; recon-12: three float4 planes
     static constexpr int kPlanes = kRecon == 18 ? 9 : 3;
     static constexpr size_t kBytesPerLink = kRecon * 4;
+    // recon-18: nine float2; recon-12: three float4 (kept as six float2)
+    struct Raw {
+        float2 d[kRecon / 2];
+    };
+    __device__ __forceinline__ static Raw fetch(const GaugeView &g, int block, int i)
+    {
+        Raw r;
+        if (kRecon == 18) {
+            const float2 *p = static_cast<const float2 *>(g.data) + (size_t)block * kPlanes * g.stride + i;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) r.d[k] = __ldg(p + (size_t)k * g.stride);
+        } else {
+            const float4 *p = static_cast<const float4 *>(g.data) + (size_t)block * kPlanes * g.stride + i;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float4 d = __ldg(p + (size_t)k * g.stride);
+                r.d[2 * k] = make_float2(d.x, d.y);
+                r.d[2 * k + 1] = make_float2(d.z, d.w);
+            }
+        }
+        return r;
+    }
+    __device__ __forceinline__ static Link<R> decode(const Raw &r)
+    {
+        Link<R> u;
+#pragma unroll
+        for (int k = 0; k < kRecon / 2; ++k) u.m[k / 3][k % 3] = mk(r.d[k].x, r.d[k].y);
+        reconstruct_row2<kRecon>(u);
+        return u;
+    }
     __device__ __forceinline__ static Link<R> load(const GaugeView &g, int block, int i)
     {
         Link<R> u;
@@ -321,6 +485,45 @@ struct GF32 {
     }
 };
 
+// Double-float links: one float4 plane (hi.re, hi.im, lo.re, lo.im) per
+// stored complex entry (9 for recon-18, 6 for recon-12).
+template <int kRecon>
+struct GDF64 {
+    using R = df;
+    static constexpr int kRecon_ = kRecon;
+    static constexpr int kPlanes = kRecon / 2;
+    static constexpr size_t kBytesPerLink = kRecon * 8;
+    struct Raw {
+        float4 d[kPlanes];
+    };
+    __device__ __forceinline__ static Raw fetch(const GaugeView &g, int block, int i)
+    {
+        Raw r;
+        const float4 *p = static_cast<const float4 *>(g.data) + (size_t)block * kPlanes * g.stride + i;
+#pragma unroll
+        for (int k = 0; k < kPlanes; ++k) r.d[k] = __ldg(p + (size_t)k * g.stride);
+        return r;
+    }
+    __device__ __forceinline__ static Link<R> decode(const Raw &r)
+    {
+        Link<R> u;
+#pragma unroll
+        for (int k = 0; k < kPlanes; ++k) u.m[k / 3][k % 3] = cx<R>{df(r.d[k].x, r.d[k].z), df(r.d[k].y, r.d[k].w)};
+        reconstruct_row2<kRecon>(u);
+        return u;
+    }
+    __device__ __forceinline__ static Link<R> load(const GaugeView &g, int block, int i) { return decode(fetch(g, block, i)); }
+    __device__ __forceinline__ static void store(const GaugeView &g, int block, int i, const Link<R> &u)
+    {
+        float4 *p = static_cast<float4 *>(g.data) + (size_t)block * kPlanes * g.stride + i;
+#pragma unroll
+        for (int k = 0; k < kPlanes; ++k) {
+            const cx<R> a = u.m[k / 3][k % 3];
+            p[(size_t)k * g.stride] = make_float4(a.re.hi, a.im.hi, a.re.lo, a.im.lo);
+        }
+    }
+};
+
 // 16-bit links (FP16 or BF16), unscaled (|U_ab| <= 1).  recon-18: nine
 // 4-byte planes (one complex); recon-12: three 8-byte planes (two complex).
 template <typename H, int kRecon>
@@ -329,6 +532,39 @@ struct G16 {
     static constexpr int kRecon_ = kRecon;
     static constexpr int kPlanes = kRecon == 18 ? 9 : 3;
     static constexpr size_t kBytesPerLink = kRecon * 2;
+    // one 32-bit word (two 16-bit reals) per complex entry
+    struct Raw {
+        uint32_t w[kRecon / 2];
+    };
+    __device__ __forceinline__ static Raw fetch(const GaugeView &g, int block, int i)
+    {
+        Raw r;
+        if (kRecon == 18) {
+            const uint32_t *p = static_cast<const uint32_t *>(g.data) + (size_t)block * kPlanes * g.stride + i;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) r.w[k] = __ldg(p + (size_t)k * g.stride);
+        } else {
+            const uint2 *p = static_cast<const uint2 *>(g.data) + (size_t)block * kPlanes * g.stride + i;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const uint2 w = __ldg(p + (size_t)k * g.stride);
+                r.w[2 * k] = w.x;
+                r.w[2 * k + 1] = w.y;
+            }
+        }
+        return r;
+    }
+    __device__ __forceinline__ static Link<R> decode(const Raw &r)
+    {
+        Link<R> u;
+#pragma unroll
+        for (int k = 0; k < kRecon / 2; ++k) {
+            const float2 f = Half16<H>::to2(r.w[k]);
+            u.m[k / 3][k % 3] = mk(f.x, f.y);
+        }
+        reconstruct_row2<kRecon>(u);
+        return u;
+    }
     __device__ __forceinline__ static Link<R> load(const GaugeView &g, int block, int i)
     {
         Link<R> u;

@@ -327,7 +327,7 @@ extern "C" qcd_status qcd_solve_cg(const qcd_gauge *g, qcd_spinor *x, const qcd_
     if (!(prm->tol > 0.0) || prm->maxiter < 1 || !std::isfinite(prm->kappa) || !std::isfinite(prm->mu))
         return fail(QCD_ERR_INVALID_ARG, "solve_cg: bad tol/maxiter/kappa/mu");
     if (prm->eo && prm->normal) return fail(QCD_ERR_INVALID_ARG, "solve_cg: normal = 1 needs eo = 0");
-    if (prm->inner_prec < QCD_PREC_F64 || prm->inner_prec > QCD_PREC_BF16)
+    if (prm->inner_prec < QCD_PREC_F64 || prm->inner_prec > QCD_PREC_DF64)
         return fail(QCD_ERR_INVALID_ARG, "solve_cg: bad inner_prec");
     const bool mixed = prm->inner_prec != QCD_PREC_F64;
     if (mixed && prm->inner_recon != 18 && prm->inner_recon != 12)
@@ -337,7 +337,9 @@ extern "C" qcd_status qcd_solve_cg(const qcd_gauge *g, qcd_spinor *x, const qcd_
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int sp = prm->inner_prec;
-    const int srecon = mixed ? prm->inner_recon : g->recon;
+    // DF64 links are kept at 18 reals (rebuilding a row in double-float
+    // arithmetic costs more than the bytes it saves)
+    const int srecon = !mixed ? g->recon : (sp == QCD_PREC_DF64 ? 18 : prm->inner_recon);
     qcd_status st;
     const GaugeView Uh = gauge_view(g, QCD_PREC_F64, g->recon, s, &st);
     if (st != QCD_OK) return st;
@@ -367,7 +369,7 @@ extern "C" qcd_status qcd_solve_cg(const qcd_gauge *g, qcd_spinor *x, const qcd_
         qs = ws_field(lat, "cg_qs", nh, sp);
         ts = ws_field(lat, "cg_ts", 1, sp);
         ss = ws_field(lat, "cg_ss", nh, sp);
-        xs = ws_field(lat, "cg_xs", nh, QCD_PREC_F32);
+        xs = ws_field(lat, "cg_xs", nh, sp == QCD_PREC_DF64 ? QCD_PREC_DF64 : QCD_PREC_F32);
         if (!rs.hv[0].data || !ps.hv[0].data || !qs.hv[0].data || !ts.hv[0].data || !ss.hv[0].data ||
             !xs.hv[0].data)
             return fail(QCD_ERR_OOM, "solve_cg: workspace");

@@ -18,7 +18,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libqcd.so")
 
-PREC = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
+PREC = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3, "df64": 4}
 PARITY = {"even": 0, "odd": 1, "full": 2}
 STATUS = {0: "QCD_OK", 1: "QCD_ERR_INVALID_ARG", 2: "QCD_ERR_OOM", 3: "QCD_ERR_CUDA",
           4: "QCD_ERR_NOT_CONVERGED", 5: "QCD_ERR_BREAKDOWN", 6: "QCD_ERR_TIMEOUT"}
@@ -43,7 +43,7 @@ class ProfileEntry(ctypes.Structure):
 
 
 class Profile(ctypes.Structure):
-    _fields_ = [("prec", ProfileEntry * 4)]
+    _fields_ = [("prec", ProfileEntry * 5)]
 
 
 # name -> (restype, argtypes); mirrors include/qcd.h
@@ -302,7 +302,7 @@ def profile_end():
     pr = Profile()
     _check(lib().qcd_profile_end(ctypes.byref(pr)), "qcd_profile_end")
     inv = {v: k for k, v in PREC.items()}
-    return {inv[i]: {k: getattr(pr.prec[i], k) for k, _ in ProfileEntry._fields_} for i in range(4)}
+    return {inv[i]: {k: getattr(pr.prec[i], k) for k, _ in ProfileEntry._fields_} for i in range(5)}
 
 
 def kernel_launches() -> int:

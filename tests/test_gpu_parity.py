@@ -388,3 +388,75 @@ def test_profile_accounting(q):
     n0 = q.kernel_launches()
     q.apply_dslash(g, so, si)
     assert q.kernel_launches() == n0 + 1
+
+
+# --------------------------------------------------------- double-float (DF64)
+
+def test_df64_roundtrip_48_bits(q):
+    dims = (6, 4, 2, 8)
+    lat, _, _ = gauge(q, dims)
+    psi = syn.gaussian_spinor(dims, 21)
+    s = q.Spinor(lat, "full", "df64")
+    s.upload(psi)
+    back = s.download()
+    # hi = RN(d), lo = RN(d - hi): |d - (hi + lo)| <= 2^-48 |d| per real part
+    assert np.all(np.abs((back - psi).real) <= 2.0 ** -48 * np.abs(psi.real))
+    assert np.all(np.abs((back - psi).imag) <= 2.0 ** -48 * np.abs(psi.imag))
+
+
+@pytest.mark.parametrize("dims", DIMS)
+@pytest.mark.parametrize("dagger", [False, True])
+def test_dslash_eo_df64(q, dims, dagger):
+    """Double-float Dslash from FP64 data: within the FP64 target 1e-13."""
+    lat, U, g = gauge(q, dims)
+    psi = syn.gaussian_spinor(dims, 22)
+    for out_par in (0, 1):
+        half_in = syn.to_half(psi, 1 - out_par)
+        want = oracle.dhop_eo(U, half_in, out_par, dagger=dagger)
+        si = q.Spinor(lat, "odd" if out_par == 0 else "even", "df64")
+        so = q.Spinor(lat, "even" if out_par == 0 else "odd", "df64")
+        si.upload(half_in)
+        q.apply_dslash(g, so, si, dagger=dagger)
+        err = F.rel_err(so.download(), want)
+        assert err <= 1e-13, err
+
+
+@pytest.mark.parametrize("kappa,mu", [(0.155, 0.0), (0.16, 0.01)])
+def test_apply_m_df64(q, kappa, mu):
+    dims = (8, 6, 4, 10)
+    lat, U, g = gauge(q, dims)
+    psi = syn.gaussian_spinor(dims, 23)
+    si, so = q.Spinor(lat, "full", "df64"), q.Spinor(lat, "full", "df64")
+    si.upload(psi)
+    for dagger in (False, True):
+        q.apply_M(g, so, si, kappa, mu, eo=False, dagger=dagger)
+        assert F.rel_err(so.download(), oracle.apply_m(U, psi, kappa, mu, dagger=dagger)) <= 1e-13
+        xe = syn.to_half(psi, 0)
+        ei, eo_ = q.Spinor(lat, "even", "df64"), q.Spinor(lat, "even", "df64")
+        ei.upload(xe)
+        q.apply_M(g, eo_, ei, kappa, mu, eo=True, dagger=dagger)
+        assert F.rel_err(eo_.download(), oracle.apply_mhat(U, xe, kappa, mu, dagger=dagger)) <= 1e-13
+
+
+@pytest.mark.parametrize("kappa,mu", [(0.155, 0.0), (0.16, 0.01)])
+def test_solve_df64_inner(q, kappa, mu):
+    """CG iterating in double-float, FP64 reliable updates (delta = 1e-5)."""
+    dims = (8, 8, 8, 4)
+    lat, U, g = gauge(q, dims, eps=0.2, seed=77)
+    b = syn.gaussian_spinor(dims, 78)
+    x, bs = q.Spinor(lat, "full", "f64"), q.Spinor(lat, "full", "f64")
+    bs.upload(b)
+    status, st = q.solve_cg(g, x, bs, kappa, mu, tol=1e-10, eo=True, inner_prec="df64", reliable_delta=1e-5)
+    assert status == 0 and st["true_rel_residual"] <= 1e-10
+    assert 1 <= st["reliable_updates"] <= 4
+    xg = x.download()
+    assert schur_residual_oracle(U, b, xg, kappa, mu) <= 1.5e-10
+    xo, _ = oracle.solve_eo(U, b, kappa, mu, tol=1e-12)
+    assert F.rel_err(xg, xo) <= 1e-7
+
+
+def test_df64_recon12_rejected(q):
+    lat, U, g = gauge(q, (4, 4, 4, 4), recon=12)
+    si, so = q.Spinor(lat, "odd", "df64"), q.Spinor(lat, "even", "df64")
+    with pytest.raises(q.QcdError):
+        q.apply_dslash(g, so, si)
