@@ -154,6 +154,15 @@ qcd_status qcd_spinor_convert(qcd_spinor *dst, const qcd_spinor *src, void *stre
 qcd_status qcd_spinor_norm2(const qcd_spinor *s, double *result_device, void *stream);
 void qcd_spinor_destroy(qcd_spinor *s);
 
+/* out[k] = D_hop in[k] (dagger: D_hop^dagger in[k]) for k < nrhs (1..32): the
+ * same parity rules as qcd_apply_dslash, all fields of one precision.  The
+ * right-hand sides are gathered into one batched field (the rhs index
+ * fastest inside each plane) so that a single launch reads each link once
+ * for all of them; the results are scattered back.  Errors: INVALID_ARG;
+ * OOM; CUDA. */
+qcd_status qcd_apply_dslash_multi(const qcd_gauge *g, qcd_spinor *const *out, const qcd_spinor *const *in, int nrhs,
+                                  int dagger, void *stream);
+
 /* |x|^2 = sum_i x[i]^2 of n doubles at x_device (e.g. the planes of an F64
  * spinor field), written to result_device (1 double), in FP64 with a fixed
  * summation order -- the reduction of qcd_spinor_norm2 without any
@@ -227,6 +236,17 @@ typedef struct {
  * (maxiter; x and stats written), BREAKDOWN, INVALID_ARG, OOM or CUDA. */
 qcd_status qcd_solve_cg(const qcd_gauge *g, qcd_spinor *x, const qcd_spinor *b, const qcd_solver_params *params,
                         qcd_solver_stats *stats, void *stream);
+
+/* nrhs (1..32) systems with the same gauge field and parameters, solved by
+ * one batched CG (the spec batching of many sources): every hopping
+ * launch reads each link once for all right-hand sides; each system keeps
+ * its own alpha, beta and convergence and stops changing once its FP64 true
+ * residual meets tol.  x[k], b[k] as for qcd_solve_cg; stats[k] per system
+ * (iterations = the iteration at which system k was solved).  The status is
+ * OK only when every system converged.  nrhs is padded to a power of two
+ * with zero systems internally. */
+qcd_status qcd_solve_cg_multi(const qcd_gauge *g, qcd_spinor *const *x, const qcd_spinor *const *b, int nrhs,
+                              const qcd_solver_params *params, qcd_solver_stats *stats, void *stream);
 
 /* ------------------------------------------------------------ measurement */
 

@@ -1,6 +1,7 @@
 // C ABI of libqcd: handles, host<->device transfer, operator application.
 // Declarations and argument conventions are in include/qcd.h.
 #include <atomic>
+#include <cstdlib>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -111,6 +112,13 @@ void *workspace(const qcd_lattice *lat, const std::string &name, size_t bytes)
     auto it = lat->ws.find(name);
     if (it != lat->ws.end() && it->second.second >= bytes) return it->second.first;
     if (it != lat->ws.end()) {
+        // cached CG graphs may hold this buffer's address: drop them all
+        cudaDeviceSynchronize();
+        for (auto &kv : lat->graphs) {
+            cudaGraphExecDestroy(kv.second.exec);
+            cudaGraphDestroy(kv.second.graph);
+        }
+        lat->graphs.clear();
         cudaFree(it->second.first);
         lat->ws.erase(it);
     }
@@ -129,6 +137,7 @@ FieldView view_half(const qcd_spinor *s, int half)
     f.nh = 1;
     f.h = s->lat->h;
     f.prec = s->prec;
+    f.rhs_log2 = 0;
     f.hv[0].data = static_cast<char *>(s->data) + half * s->half_data_bytes;
     f.hv[0].norm = s->norm ? reinterpret_cast<float *>(reinterpret_cast<char *>(s->norm) + half * s->half_norm_bytes)
                            : nullptr;
@@ -147,24 +156,28 @@ FieldView view_of(const qcd_spinor *s)
     return f;
 }
 
-FieldView ws_field(const qcd_lattice *lat, const std::string &name, int nh, int prec)
+FieldView ws_field(const qcd_lattice *lat, const std::string &name, int nh, int prec, int rhs_log2)
 {
-    const size_t db = spinor_half_bytes(prec, lat->stride), nb = spinor_half_norm_bytes(prec, lat->stride);
-    char *base = static_cast<char *>(workspace(lat, name + "/p" + std::to_string(prec), nh * (db + nb)));
+    const int ne = lat->h << rhs_log2;
+    const int stride = rhs_log2 == 0 ? lat->stride : (ne + 63) / 64 * 64;
+    const size_t db = spinor_half_bytes(prec, stride), nb = spinor_half_norm_bytes(prec, stride);
+    char *base = static_cast<char *>(
+        workspace(lat, name + "/p" + std::to_string(prec) + "/n" + std::to_string(rhs_log2), nh * (db + nb)));
     FieldView f;
     f.nh = nh;
-    f.h = lat->h;
+    f.h = ne;
     f.prec = prec;
+    f.rhs_log2 = rhs_log2;
     for (int k = 0; k < 2; ++k) {
         const int kk = k < nh ? k : 0;
         f.hv[k].data = base ? base + kk * db : nullptr;
         f.hv[k].norm = (base && nb) ? reinterpret_cast<float *>(base + nh * db + kk * nb) : nullptr;
-        f.hv[k].stride = lat->stride;
+        f.hv[k].stride = stride;
     }
     return f;
 }
 
-Reduction reduction_of(const qcd_lattice *lat) { return Reduction{lat->red_partials, lat->red_counter}; }
+Reduction reduction_of(const qcd_lattice *lat) { return Reduction{lat->red_partials, lat->red_counter, lat->red_cap}; }
 
 GaugeView gauge_view(const qcd_gauge *g, int prec, int recon, cudaStream_t s, qcd_status *st)
 {
@@ -247,6 +260,113 @@ cudaError_t launch_dslash(int prec, int recon, const DslashLaunch &a, cudaStream
     }
 }
 
+// ---- autotuner of the hopping-kernel block size
+//
+// The paper compiles its kernels for the lattice at hand and keeps the
+// compiled binaries for later runs (Sec. 4).  Here the kernels are compiled
+// ahead of time; what depends on the lattice is the launch shape.  The
+// first launch of a (precision, recon, batch, parity layout, extents)
+// configuration outside stream capture times the FP32/16-bit kernel with 64,
+// 128 and 256 threads per block (CUDA events, three launches each on
+// scratch fields) and keeps the fastest.  With QCD_TUNE_CACHE=<file> the
+// choices are read from and appended to that file, so later processes skip
+// the timing.
+static std::mutex g_tune_mu;
+static std::map<std::string, int> g_tune;
+static bool g_tune_loaded = false;
+
+static void tune_load()
+{
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char *path = getenv("QCD_TUNE_CACHE");
+    if (!path) return;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    char key[256];
+    int v;
+    while (fscanf(f, "%255s %d", key, &v) == 2)
+        if (v == 64 || v == 128 || v == 256) g_tune[key] = v;
+    fclose(f);
+}
+
+static void tune_store(const std::string &key, int v)
+{
+    g_tune[key] = v;
+    const char *path = getenv("QCD_TUNE_CACHE");
+    if (!path) return;
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s %d\n", key.c_str(), v);
+    fclose(f);
+}
+
+static std::string tune_key(const qcd_lattice *lat, int prec, int recon, int L, bool both)
+{
+    char k[160];
+    snprintf(k, sizeof(k), "dslash:p%d:r%d:n%d:b%d:%dx%dx%dx%d", prec, recon, L, both ? 1 : 0, lat->dims[0], lat->dims[1],
+             lat->dims[2], lat->dims[3]);
+    return k;
+}
+
+int tuned_tpb(const qcd_lattice *lat, const GaugeView &U, int prec, int recon, int L, bool both, cudaStream_t s)
+{
+    if (prec == QCD_PREC_F64 || prec == QCD_PREC_DF64) return 64;
+    const std::string key = tune_key(lat, prec, recon, L, both);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_load();
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) return it->second;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return 128;
+    const FieldView ti = ws_field(lat, "tune_in", both ? 2 : 1, prec, L);
+    const FieldView to = ws_field(lat, "tune_out", both ? 2 : 1, prec, L);
+    if (!ti.hv[0].data || !to.hv[0].data || launch_zero(ti, s) != cudaSuccess) return 128;
+    DslashLaunch a;
+    memset(&a, 0, sizeof(a));
+    a.g = lat->geom;
+    a.both = both ? 1 : 0;
+    a.rhs_log2 = L;
+    a.U = U;
+    for (int p = 0; p < 2; ++p) {
+        a.out[p] = to.hv[both ? p : 0];
+        a.in[p] = ti.hv[both ? 1 - p : 0];
+    }
+    a.epi = EPI_PLAIN;
+    a.state = lat->state;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = 128;
+    float best_ms = 1e30f;
+    for (int tpb : {128, 64, 256}) {
+        a.tpb = tpb;
+        bool ok = launch_dslash(prec, recon, a, s) == cudaSuccess;  // warm-up
+        float ms_min = 1e30f;
+        for (int r = 0; r < 3 && ok; ++r) {
+            cudaEventRecord(e0, s);
+            ok = launch_dslash(prec, recon, a, s) == cudaSuccess;
+            cudaEventRecord(e1, s);
+            float ms = 0.f;
+            if (ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+                ms_min = ms < ms_min ? ms : ms_min;
+        }
+        note_launches(4);
+        if (ok && ms_min < best_ms) {
+            best_ms = ms_min;
+            best = tpb;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGetLastError();
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_store(key, best);
+    return best;
+}
+
 cudaError_t hop(const qcd_lattice *lat, const GaugeView &U, int recon, const HopArgs &h, cudaStream_t s)
 {
     DslashLaunch a;
@@ -254,6 +374,7 @@ cudaError_t hop(const qcd_lattice *lat, const GaugeView &U, int recon, const Hop
     a.g = lat->geom;
     a.out_parity = h.out_parity;
     a.both = h.both ? 1 : 0;
+    a.rhs_log2 = h.out->rhs_log2;
     a.dagger = h.dagger;
     a.U = U;
     if (h.both) {
@@ -276,8 +397,14 @@ cudaError_t hop(const qcd_lattice *lat, const GaugeView &U, int recon, const Hop
         a.epi = EPI_CPLX_D;  // out = cd .* D in (real coefficients are the im = 0 case)
     else
         a.epi = h.twisted ? EPI_CPLX_YD : EPI_REAL_YD;
+    a.tpb = tuned_tpb(lat, U, h.out->prec, recon, h.out->rhs_log2, h.both, s);
     a.reduce = h.reduce;
-    a.red = reduction_of(lat);
+    a.red = h.red ? *h.red : reduction_of(lat);
+    if (h.reduce) {
+        const int tpb = a.tpb;
+        const size_t blocks = (size_t)(((lat->h << h.out->rhs_log2) + tpb - 1) / tpb) * (h.both ? 2 : 1);
+        if (!reduction_fits(a.red, 1, h.out->rhs_log2, blocks)) return cudaErrorInvalidValue;
+    }
     a.fin = h.fin;
     a.state = lat->state;
     a.red_out = lat->red_out;
@@ -292,8 +419,9 @@ cudaError_t hop(const qcd_lattice *lat, const GaugeView &U, int recon, const Hop
     r.e0 = pool_event();
     r.e1 = pool_event();
     r.prec = h.out->prec;
-    r.sites = (double)lat->h * (h.both ? 2 : 1);
-    r.bytes = r.sites * (8 * link_bytes(h.out->prec, recon) + (h.y ? 3 : 2) * spinor_site_bytes(h.out->prec));
+    r.sites = (double)(lat->h << h.out->rhs_log2) * (h.both ? 2 : 1);  // site x rhs elements
+    r.bytes = (double)lat->h * (h.both ? 2 : 1) * 8 * link_bytes(h.out->prec, recon) +
+              r.sites * (h.y ? 3 : 2) * spinor_site_bytes(h.out->prec);
     r.flops = r.sites * 1320.0;
     cudaEventRecord(r.e0, s);
     note_launches();
@@ -410,6 +538,7 @@ qcd_status qcd_lattice_create(const int dims[4], int t_bc, qcd_lattice **out)
     cudaError_t e = cudaMalloc(&lat->red_partials, lat->red_cap * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&lat->red_counter, 64);
     if (e == cudaSuccess) e = cudaMalloc(&lat->red_out, 8 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&lat->red_out_big, 2 * kMaxRhs * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&lat->state, sizeof(CgState));
     if (e == cudaSuccess) e = cudaMallocHost(&lat->state_host, sizeof(CgState));
     if (e == cudaSuccess) e = cudaMemset(lat->red_counter, 0, 64);
@@ -431,6 +560,7 @@ void qcd_lattice_destroy(qcd_lattice *lat)
     cudaFree(lat->red_partials);
     cudaFree(lat->red_counter);
     cudaFree(lat->red_out);
+    cudaFree(lat->red_out_big);
     cudaFree(lat->state);
     if (lat->state_host) cudaFreeHost(lat->state_host);
     for (auto &kv : lat->ws) cudaFree(kv.second.first);
@@ -656,6 +786,48 @@ qcd_status qcd_apply_dslash(const qcd_gauge *g, qcd_spinor *out, const qcd_spino
     h.plain = true;
     h.fin = FIN_STORE;
     return check_cuda(hop(g->lat, U, g->recon, h, s), "apply_dslash");
+}
+
+qcd_status qcd_apply_dslash_multi(const qcd_gauge *g, qcd_spinor *const *out, const qcd_spinor *const *in, int nrhs,
+                                  int dagger, void *stream)
+{
+    if (!g || !out || !in) return fail(QCD_ERR_INVALID_ARG, "apply_dslash_multi: NULL argument");
+    if (nrhs < 1 || nrhs > kMaxRhs) return fail(QCD_ERR_INVALID_ARG, "apply_dslash_multi: nrhs = %d not in 1..%d", nrhs, kMaxRhs);
+    for (int k = 0; k < nrhs; ++k) {
+        if (!out[k] || !in[k]) return fail(QCD_ERR_INVALID_ARG, "apply_dslash_multi: NULL field");
+        if (out[k]->lat != g->lat || in[k]->lat != g->lat) return fail(QCD_ERR_INVALID_ARG, "apply_dslash_multi: lattices differ");
+        if (out[k]->prec != in[0]->prec || in[k]->prec != in[0]->prec || out[k]->parity != out[0]->parity ||
+            in[k]->parity != in[0]->parity)
+            return fail(QCD_ERR_INVALID_ARG, "apply_dslash_multi: fields must share precision and parity");
+        if (out[k]->data == in[k]->data) return fail(QCD_ERR_INVALID_ARG, "apply_dslash_multi: out aliases in");
+    }
+    const bool both = out[0]->parity == QCD_PARITY_FULL && in[0]->parity == QCD_PARITY_FULL;
+    if (!both && !(out[0]->parity != QCD_PARITY_FULL && in[0]->parity == 1 - out[0]->parity))
+        return fail(QCD_ERR_INVALID_ARG, "apply_dslash_multi: parities must be (EVEN, ODD), (ODD, EVEN) or (FULL, FULL)");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const qcd_lattice *lat = g->lat;
+    qcd_status st;
+    GaugeView U = gauge_view(g, in[0]->prec, g->recon, s, &st);
+    if (st != QCD_OK) return st;
+    int L = 0;
+    while ((1 << L) < nrhs) ++L;
+    const int nh = both ? 2 : 1, prec = in[0]->prec;
+    const FieldView bi = ws_field(lat, "dm_in", nh, prec, L), bo = ws_field(lat, "dm_out", nh, prec, L);
+    if (!bi.hv[0].data || !bo.hv[0].data) return fail(QCD_ERR_OOM, "apply_dslash_multi: workspace");
+    cudaError_t e = launch_zero(bi, s);
+    for (int k = 0; k < nrhs && e == cudaSuccess; ++k) e = launch_batch_copy(bi, view_of(in[k]), k, 1, s);
+    if (e != cudaSuccess) return check_cuda(e, "apply_dslash_multi: gather");
+    HopArgs h{};
+    h.out = &bo;
+    h.in = &bi;
+    h.out_parity = both ? 0 : out[0]->parity;
+    h.both = both;
+    h.dagger = dagger ? 1 : 0;
+    h.plain = true;
+    h.fin = FIN_STORE;
+    e = hop(lat, U, g->recon, h, s);
+    for (int k = 0; k < nrhs && e == cudaSuccess; ++k) e = launch_batch_copy(bo, view_of(out[k]), k, 0, s);
+    return check_cuda(e, "apply_dslash_multi");
 }
 
 qcd_status qcd_apply_M(const qcd_gauge *g, qcd_spinor *out, const qcd_spinor *in, double kappa, double mu, int eo,

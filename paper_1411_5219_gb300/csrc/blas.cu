@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kThreads) norm2_kernel(const FieldView f, cons
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     double v[1] = {0.0};
     if (k < nsites(f)) v[0] = (double)norm2(ld<SF>(f, k));
-    grid_reduce<1>(v, red, fin, stt, out);
+    grid_reduce_rhs<1>(v, f.rhs_log2, red, fin, stt, out);
 }
 
 __global__ void __launch_bounds__(kThreads) diff_norm2_kernel(const FieldView a, const FieldView b, const Reduction red,
@@ -117,13 +117,19 @@ __global__ void __launch_bounds__(kThreads) diff_norm2_kernel(const FieldView a,
                 v[1] += y.c[s][c].re * y.c[s][c].re + y.c[s][c].im * y.c[s][c].im;
             }
     }
-    grid_reduce<2>(v, red, FIN_STORE, nullptr, out);
+    grid_reduce_rhs<2>(v, a.rhs_log2, red, FIN_STORE, nullptr, out);
 }
 
-__global__ void cg_state_init_kernel(CgState *s, double tol2, double delta2, int maxiter)
+__global__ void cg_state_init_kernel(CgState *s, int nrhs, double tol2, double delta2, int maxiter)
 {
-    s->rr = s->rr_prev = s->pAp = s->alpha = s->beta = 0.0;
-    s->rr_stop = s->rr_max = s->rr_true = 0.0;
+    for (int k = 0; k < kMaxRhs; ++k) {
+        CgRhs &q = s->r[k];
+        q.rr = q.rr_prev = q.pAp = q.alpha = q.beta = 0.0;
+        q.rr_stop = q.rr_max = q.rr_true = q.b2 = 0.0;
+        q.status = CG_DONE;
+        q.iter_done = 0;
+    }
+    s->nrhs = nrhs;
     s->tol2 = tol2;
     s->delta2 = delta2;
     s->iter = 0;
@@ -167,7 +173,7 @@ __global__ void __launch_bounds__(kThreads) cg_setup_kernel(const FieldView rhs,
         if (has_xs) st<SS>(xs, k, zero_spinor<typename SS::R>());
         v[0] = norm2(b);
     }
-    grid_reduce<1>(v, red, FIN_CG_INIT, stt, nullptr);
+    grid_reduce_rhs<1>(v, rhs.rhs_log2, red, FIN_CG_INIT, stt, nullptr);
 }
 
 // x += alpha p; r -= alpha q; |r|^2.
@@ -181,7 +187,7 @@ __global__ void __launch_bounds__(kThreads) cg_xr_kernel(const FieldView x, cons
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     double v[1] = {0.0};
     if (k < nsites(x)) {
-        const double alpha = stt->alpha;
+        const double alpha = stt->r[k & ((1 << x.rhs_log2) - 1)].alpha;
         const Spinor<R> pp = ld<SF>(p, k), qq = ld<SF>(q, k);
         Spinor<R> rr = ld<SF>(r, k);
         Spinor<RX> xx = ld<SX>(x, k);
@@ -200,7 +206,7 @@ __global__ void __launch_bounds__(kThreads) cg_xr_kernel(const FieldView x, cons
         st<SF>(r, k, rr);
         v[0] = (double)norm2(rr);
     }
-    grid_reduce<1>(v, red, FIN_CG_RR, stt, nullptr);
+    grid_reduce_rhs<1>(v, x.rhs_log2, red, FIN_CG_RR, stt, nullptr);
 }
 
 // p = r + beta p
@@ -211,7 +217,7 @@ __global__ void __launch_bounds__(kThreads) cg_p_kernel(const FieldView p, const
     using R = typename SF::R;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nsites(p)) return;
-    const R beta = (R)stt->beta;
+    const R beta = (R)stt->r[k & ((1 << p.rhs_log2) - 1)].beta;
     Spinor<R> pp = ld<SF>(p, k);
     const Spinor<R> rr = ld<SF>(r, k);
 #pragma unroll
@@ -260,7 +266,22 @@ __global__ void __launch_bounds__(kThreads) cg_true_residual_kernel(const FieldV
         if (has_rs) st<SS>(rs, k, cvt<typename SS::R>(a));
         v[0] = norm2(a);
     }
-    grid_reduce<1>(v, red, FIN_CG_TRUE, stt, nullptr);
+    grid_reduce_rhs<1>(v, rhs.rhs_log2, red, FIN_CG_TRUE, stt, nullptr);
+}
+
+// batched[(i << L) | rhs] <-> plain[i] over both halves
+template <typename SF>
+__global__ void __launch_bounds__(kThreads) batch_copy_kernel(const FieldView b, const FieldView pl, const int rhs,
+                                                              const int to_batch)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nsites(pl)) return;
+    const int hh = k >= pl.h, i = k - hh * pl.h;
+    const int e = (i << b.rhs_log2) | rhs;
+    if (to_batch)
+        SF::store(b.hv[hh], e, SF::load(pl.hv[hh], i));
+    else
+        SF::store(pl.hv[hh], i, SF::load(b.hv[hh], e));
 }
 
 }  // namespace
@@ -302,6 +323,15 @@ cudaError_t launch_convert(const FieldView &dst, const FieldView &src, cudaStrea
     return cudaGetLastError();
 }
 
+cudaError_t launch_batch_copy(const FieldView &batched, const FieldView &plain, int rhs, int to_batch, cudaStream_t s)
+{
+    if (batched.prec != plain.prec || batched.nh != plain.nh) return cudaErrorInvalidValue;
+    QCD_SP_CASES(plain.prec, SF,
+                 batch_copy_kernel<SF><<<grid_of(plain), kThreads, 0, s>>>(batched, plain, rhs, to_batch));
+    note_launches();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_zero(const FieldView &f, cudaStream_t s)
 {
     QCD_SP_CASES(f.prec, SF, zero_kernel<SF><<<grid_of(f), kThreads, 0, s>>>(f));
@@ -320,6 +350,7 @@ cudaError_t launch_twist(const FieldView &out, const FieldView &in, const double
 cudaError_t launch_norm2(const FieldView &f, const Reduction &red, FinalizeKind fin, CgState *stt, double *out,
                          cudaStream_t s)
 {
+    if (!reduction_fits(red, 1, f.rhs_log2, grid_of(f).x)) return cudaErrorInvalidValue;
     QCD_SP_CASES(f.prec, SF, norm2_kernel<SF><<<grid_of(f), kThreads, 0, s>>>(f, red, fin, stt, out));
     note_launches();
     return cudaGetLastError();
@@ -328,14 +359,15 @@ cudaError_t launch_norm2(const FieldView &f, const Reduction &red, FinalizeKind 
 cudaError_t launch_diff_norm2(const FieldView &a, const FieldView &b, const Reduction &red, double *out, cudaStream_t s)
 {
     if (a.prec != QCD_PREC_F64 || b.prec != QCD_PREC_F64) return cudaErrorInvalidValue;
+    if (!reduction_fits(red, 2, a.rhs_log2, grid_of(a).x)) return cudaErrorInvalidValue;
     diff_norm2_kernel<<<grid_of(a), kThreads, 0, s>>>(a, b, red, out);
     note_launches();
     return cudaGetLastError();
 }
 
-cudaError_t launch_cg_state_init(CgState *stt, double tol2, double delta2, int maxiter, cudaStream_t s)
+cudaError_t launch_cg_state_init(CgState *stt, int nrhs, double tol2, double delta2, int maxiter, cudaStream_t s)
 {
-    cg_state_init_kernel<<<1, 1, 0, s>>>(stt, tol2, delta2, maxiter);
+    cg_state_init_kernel<<<1, 1, 0, s>>>(stt, nrhs, tol2, delta2, maxiter);
     note_launches();
     return cudaGetLastError();
 }
@@ -359,6 +391,7 @@ cudaError_t launch_cg_setup(const FieldView &rhs, const FieldView &r, const Fiel
 {
     const FieldView xsv = xs ? *xs : x;
     const bool has = xs != nullptr;
+    if (!reduction_fits(red, 1, rhs.rhs_log2, grid_of(rhs).x)) return cudaErrorInvalidValue;
     if (x.prec == QCD_PREC_F64 && r.prec == QCD_PREC_F64 && !has) {
         cg_setup_kernel<SpF64, SpF64, SpF32><<<grid_of(rhs), kThreads, 0, s>>>(rhs, r, p, x, xsv, false, red, stt);
     } else if (x.prec == QCD_PREC_F64 && has && xs->prec == QCD_PREC_DF64 && r.prec == QCD_PREC_DF64) {
@@ -376,6 +409,7 @@ cudaError_t launch_cg_setup(const FieldView &rhs, const FieldView &r, const Fiel
 cudaError_t launch_cg_xr(const FieldView &x, const FieldView &p, const FieldView &r, const FieldView &q,
                          const Reduction &red, CgState *stt, cudaStream_t s)
 {
+    if (!reduction_fits(red, 1, x.rhs_log2, grid_of(x).x)) return cudaErrorInvalidValue;
     if (x.prec == QCD_PREC_F64 && p.prec == QCD_PREC_F64) {
         cg_xr_kernel<SpF64, SpF64><<<grid_of(x), kThreads, 0, s>>>(x, p, r, q, red, stt);
     } else if (x.prec == QCD_PREC_DF64 && p.prec == QCD_PREC_DF64) {
@@ -406,6 +440,7 @@ cudaError_t launch_cg_accum_x(const FieldView &xhi, const FieldView &xs, cudaStr
 cudaError_t launch_cg_true_residual(const FieldView &rhs, const FieldView &q, const FieldView &rhi, const FieldView *rs,
                                     const Reduction &red, CgState *stt, cudaStream_t s)
 {
+    if (!reduction_fits(red, 1, rhs.rhs_log2, grid_of(rhs).x)) return cudaErrorInvalidValue;
     if (!rs) {
         cg_true_residual_kernel<SpF64><<<grid_of(rhs), kThreads, 0, s>>>(rhs, q, rhi, rhi, false, red, stt);
     } else {

@@ -170,19 +170,22 @@ __host__ __device__ constexpr int dslash_min_blocks()
     return sizeof(typename SF::R) == 8 ? 6 : 1;
 }
 
-template <typename SF, typename GF, int kDagger, int kEpi, bool kReduce>
-__global__ void __launch_bounds__(dslash_tpb<SF>(), dslash_min_blocks<SF>()) dslash_kernel(const DslashLaunch a)
+template <typename SF, typename GF, int kDagger, int kEpi, bool kReduce, int TPB>
+__global__ void __launch_bounds__(TPB, TPB == 64 ? dslash_min_blocks<SF>() : 1) dslash_kernel(const DslashLaunch a)
 {
     using R = typename SF::R;
     if (a.check_status && a.state->status != CG_RUNNING) return;
     constexpr int SF_ = kDagger ? -1 : +1;  // projector sign of forward hops
     constexpr int SB_ = -SF_;                // ... of backward hops
-    constexpr int TPB = dslash_tpb<SF>();
-    const int nbp = (a.g.h + TPB - 1) / TPB;
+    // element e = site i * 2^rhs_log2 + rhs (one rhs: e = i)
+    const int ne = a.g.h << a.rhs_log2;
+    const int nbp = (ne + TPB - 1) / TPB;
     const int p = a.both ? (int)(blockIdx.x >= (unsigned)nbp) : a.out_parity;
-    const int i = (blockIdx.x - (a.both ? p * nbp : 0)) * blockDim.x + threadIdx.x;
+    const int e = (blockIdx.x - (a.both ? p * nbp : 0)) * blockDim.x + threadIdx.x;
+    const int L = a.rhs_log2, rhs = e & ((1 << L) - 1);
+    const int i = e >> L;
     double red[1] = {0.0};
-    if (i < a.g.h) {
+    if (e < ne) {
         const Geom &g = a.g;
         const SpinorView &in = a.in[p];
         const SiteCoords c = site_coords(g, i, p);
@@ -209,6 +212,7 @@ __global__ void __launch_bounds__(dslash_tpb<SF>(), dslash_min_blocks<SF>()) dsl
             for (int k = 0; k < 8; ++k) {
                 lb[k] = (k & 1 ? bwd : fwd) + (k >> 1);
                 li[k] = k & 1 ? nb[k] : i;
+                nb[k] = (nb[k] << L) | rhs;  // neighbour element of the same rhs
                 fl[k] = false;
             }
             fl[6] = anti && wf;
@@ -253,7 +257,7 @@ __global__ void __launch_bounds__(dslash_tpb<SF>(), dslash_min_blocks<SF>()) dsl
 #pragma unroll
                 for (int cc = 0; cc < 3; ++cc) out.c[s][cc] = d * acc.c[s][cc];
         } else if (kEpi == EPI_REAL_YD) {
-            const Spinor<R> y = SF::load(a.y[p], i);
+            const Spinor<R> y = SF::load(a.y[p], e);
             const R cy = (R)a.cy[0][0], d = (R)a.cd[0][0];
 #pragma unroll
             for (int s = 0; s < 4; ++s)
@@ -270,7 +274,7 @@ __global__ void __launch_bounds__(dslash_tpb<SF>(), dslash_min_blocks<SF>()) dsl
 #pragma unroll
                     for (int cc = 0; cc < 3; ++cc) out.c[s][cc] = cmul(d[s >> 1], acc.c[s][cc]);
             } else {
-                const Spinor<R> y = SF::load(a.y[p], i);
+                const Spinor<R> y = SF::load(a.y[p], e);
                 const cx<R> cy[2] = {mk((R)a.cy[0][0], (R)a.cy[0][1]), mk((R)a.cy[1][0], (R)a.cy[1][1])};
 #pragma unroll
                 for (int s = 0; s < 4; ++s)
@@ -278,7 +282,7 @@ __global__ void __launch_bounds__(dslash_tpb<SF>(), dslash_min_blocks<SF>()) dsl
                     for (int cc = 0; cc < 3; ++cc) out.c[s][cc] = cmac(cmul(cy[s >> 1], y.c[s][cc]), d[s >> 1], acc.c[s][cc]);
             }
         }
-        SF::store(a.out[p], i, out);
+        SF::store(a.out[p], e, out);
         if (kReduce) {
             R n = 0;
 #pragma unroll
@@ -288,20 +292,19 @@ __global__ void __launch_bounds__(dslash_tpb<SF>(), dslash_min_blocks<SF>()) dsl
             red[0] = (double)n;
         }
     }
-    if (kReduce) grid_reduce<1>(red, a.red, a.fin, a.state, a.red_out);
+    if (kReduce) grid_reduce_rhs<1>(red, a.rhs_log2, a.red, a.fin, a.state, a.red_out);
 }
 
-// Dispatch over epilogue / reduction for one format pair and one dagger
-// value.  (The real-scale epilogue without y has no caller and is not
-// instantiated.)
-template <typename SF, typename GF, int D>
-cudaError_t launch_dslash_dag(const DslashLaunch &a, cudaStream_t s)
+// Dispatch over epilogue / reduction for one format pair, one dagger value
+// and one block size.  (The real-scale epilogue without y has no caller and
+// is not instantiated.)
+template <typename SF, typename GF, int D, int TPB>
+cudaError_t launch_dslash_tpb(const DslashLaunch &a, cudaStream_t s)
 {
-    constexpr int TPB = dslash_tpb<SF>();
-    const dim3 grid((a.g.h + TPB - 1) / TPB * (a.both ? 2 : 1)), block(TPB);
+    const dim3 grid((((a.g.h << a.rhs_log2) + TPB - 1) / TPB) * (a.both ? 2 : 1)), block(TPB);
 #define QCD_DSL(E, RD)                                                      \
     if (a.epi == E && a.reduce == RD) {                                     \
-        dslash_kernel<SF, GF, D, E, RD><<<grid, block, 0, s>>>(a);          \
+        dslash_kernel<SF, GF, D, E, RD, TPB><<<grid, block, 0, s>>>(a);     \
         return cudaGetLastError();                                          \
     }
     QCD_DSL(EPI_PLAIN, false)
@@ -311,6 +314,21 @@ cudaError_t launch_dslash_dag(const DslashLaunch &a, cudaStream_t s)
     QCD_DSL(EPI_CPLX_YD, false)
     QCD_DSL(EPI_CPLX_YD, true)
 #undef QCD_DSL
+    return cudaErrorInvalidValue;
+}
+
+// Block sizes: the FP64-family kernels (~170 registers) always use 64; the
+// FP32 / 16-bit ones take a.tpb in {64, 128, 256} (chosen by the autotuner,
+// 128 by default).
+template <typename SF, typename GF, int D>
+cudaError_t launch_dslash_dag(const DslashLaunch &a, cudaStream_t s)
+{
+    if (sizeof(typename SF::R) == 8) return launch_dslash_tpb<SF, GF, D, 64>(a, s);
+    if constexpr (sizeof(typename SF::R) != 8) {
+        if (a.tpb == 64) return launch_dslash_tpb<SF, GF, D, 64>(a, s);
+        if (a.tpb == 256) return launch_dslash_tpb<SF, GF, D, 256>(a, s);
+        return launch_dslash_tpb<SF, GF, D, 128>(a, s);
+    }
     return cudaErrorInvalidValue;
 }
 

@@ -19,6 +19,7 @@ struct qcd_lattice {
     size_t red_cap = 0;              // doubles
     unsigned *red_counter = nullptr; // ticket counter (zero between kernels)
     double *red_out = nullptr;       // FIN_STORE results (8 doubles)
+    double *red_out_big = nullptr;   // per-rhs FIN_STORE results (2 * kMaxRhs doubles)
     qcd::CgState *state = nullptr;   // device CG state
     qcd::CgState *state_host = nullptr;  // pinned mirror
     // Named workspace buffers (staging, solver fields), grown on demand.
@@ -75,7 +76,7 @@ void *workspace(const qcd_lattice *lat, const std::string &name, size_t bytes);
 // Views.
 FieldView view_of(const qcd_spinor *s);
 FieldView view_half(const qcd_spinor *s, int half);  // half of a FULL field
-FieldView ws_field(const qcd_lattice *lat, const std::string &name, int nh, int prec);
+FieldView ws_field(const qcd_lattice *lat, const std::string &name, int nh, int prec, int rhs_log2 = 0);
 GaugeView gauge_view(const qcd_gauge *g, int prec, int recon, cudaStream_t s, qcd_status *st);
 Reduction reduction_of(const qcd_lattice *lat);
 
@@ -103,7 +104,12 @@ struct HopArgs {
     bool reduce;
     FinalizeKind fin;
     bool check_status;
+    const Reduction *red;  // scratch of the fused reduction (nullptr: the lattice's)
 };
 cudaError_t hop(const qcd_lattice *lat, const GaugeView &U, int recon, const HopArgs &h, cudaStream_t s);
+
+// Autotuned threads per block of the hopping kernel for this configuration
+// (times the candidates on first use outside stream capture).
+int tuned_tpb(const qcd_lattice *lat, const GaugeView &U, int prec, int recon, int rhs_log2, bool both, cudaStream_t s);
 
 }  // namespace qcd

@@ -688,114 +688,158 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double *smem /* NV * 
 // counter; the last block to finish sums the partials in block order, so
 // the result does not depend on scheduling.
 struct Reduction {
-    double *partials;   // >= gridDim.x * NV doubles
+    double *partials;   // >= NV * nrhs * gridDim.x doubles
     unsigned *counter;  // zero before the launch; reset to zero by the last block
+    size_t cap;         // capacity of partials in doubles (checked on the host before each launch)
 };
 
-// Device-resident CG state.  Kernels of an iteration read `status` and
-// return at once when it is not RUNNING, so the host may enqueue several
-// iterations ahead without reading anything back.
+// Host check: a reducing launch of `blocks` blocks with NV values for 2^L
+// right-hand sides fits the partials buffer.
+inline bool reduction_fits(const Reduction &r, int nv, int rhs_log2, size_t blocks)
+{
+    return (size_t)nv * ((size_t)1 << rhs_log2) * blocks <= r.cap;
+}
+
+// Device-resident CG state for nrhs right-hand sides solved together.
+// Kernels of an iteration read the global `status` and return at once when
+// it is not RUNNING, so the host may enqueue iterations ahead without reading
+// anything back.  Each right-hand side keeps its own scalars: a solved one
+// gets alpha = beta = 0 and rides along unchanged.
 enum CgStatus : int {
     CG_RUNNING = 0,
-    CG_CONVERGED = 1,   // iterated residual below the target
-    CG_RELIABLE = 2,    // reliable update requested
-    CG_BREAKDOWN = 3,   // <p, A p> <= 0 or not finite
-    CG_MAXITER = 4,
-    CG_DONE = 5,        // true residual below the target: solved
+    CG_CONVERGED = 1,   // (per rhs) iterated residual below the target
+    CG_RELIABLE = 2,    // (global) an FP64 true residual is due
+    CG_BREAKDOWN = 3,   // <p, A p> <= 0 or non-finite values
+    CG_MAXITER = 4,     // (global)
+    CG_DONE = 5,        // true residual below the target
 };
 
-struct CgState {
+constexpr int kMaxRhs = 32;
+
+struct CgRhs {
     double rr;        // |r|^2 of the current iterate
-    double rr_prev;   // |r|^2 before the last update (for beta after a reliable update)
+    double rr_prev;   // |r|^2 before the last update (beta after a reliable update)
     double pAp;       // |Mhat p|^2 of this iteration
     double alpha, beta;
     double rr_stop;   // tol^2 |rhs|^2
     double rr_max;    // largest |r|^2 since the last reliable update
-    double delta2;    // reliable_delta^2 (0: no reliable updates)
-    double rr_true;   // |rhs - A x|^2 from the last true-residual computation
-    double tol2;      // tol^2
+    double rr_true;   // |rhs - A x|^2 of the last true-residual computation
     double b2;        // |rhs|^2
+    int status;       // RUNNING, DONE or BREAKDOWN
+    int iter_done;    // iteration at which it was solved
+};
+
+struct CgState {
+    CgRhs r[kMaxRhs];
+    int nrhs;
+    double tol2;      // tol^2
+    double delta2;    // reliable_delta^2 (0: true residual only at convergence)
     int iter, maxiter;
-    int status;
+    int status;       // global
     int reliable_updates;
     int trips, trip_limit;  // device-driven loop: body executions and their cap
-    unsigned counter[4];
 };
 
 // What the last block does with a finished reduction.
 enum FinalizeKind : int {
-    FIN_STORE = 0,      // out[0..NV) = totals
+    FIN_STORE = 0,      // out[k * nrhs + r] = totals
     FIN_CG_ALPHA = 1,   // pAp = total; alpha = rr / pAp (breakdown check)
     FIN_CG_RR = 2,      // rr_new = total; beta, convergence, reliable trigger
     FIN_CG_TRUE = 3,    // true residual after a reliable update
     FIN_CG_INIT = 4,    // |rhs|^2 at the start of CG
 };
 
-template <int NV>
-__device__ __forceinline__ void cg_finalize(FinalizeKind kind, const double (&tot)[NV], CgState *st, double *out)
+// tot[r] = the reduced value of right-hand side r (first value only).
+__device__ __forceinline__ void cg_finalize_rhs(FinalizeKind kind, const double *tot, CgState *st)
 {
+    const int n = st->nrhs;
     if (kind == FIN_CG_INIT) {
-        const double b2 = tot[0];
-        st->rr = st->rr_prev = st->rr_max = st->rr_true = b2;
-        st->rr_stop = st->tol2 * b2;
-        st->b2 = b2;
+        bool all_done = true, bad = false;
+        for (int k = 0; k < n; ++k) {
+            CgRhs &q = st->r[k];
+            const double b2 = tot[k];
+            q.rr = q.rr_prev = q.rr_max = q.rr_true = q.b2 = b2;
+            q.rr_stop = st->tol2 * b2;
+            q.alpha = q.beta = q.pAp = 0.0;
+            q.iter_done = 0;
+            q.status = b2 == 0.0 ? CG_DONE : CG_RUNNING;
+            all_done = all_done && q.status == CG_DONE;
+            bad = bad || !isfinite(b2);
+        }
         st->iter = 0;
         st->reliable_updates = 0;
-        st->alpha = st->beta = 0.0;
-        st->status = (b2 == 0.0) ? CG_DONE : (isfinite(b2) ? CG_RUNNING : CG_BREAKDOWN);
-    } else if (kind == FIN_STORE) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) out[k] = tot[k];
+        st->status = bad ? CG_BREAKDOWN : all_done ? CG_DONE : CG_RUNNING;
     } else if (kind == FIN_CG_ALPHA) {
-        const double pAp = tot[0];
-        st->pAp = pAp;
-        if (!(pAp > 0.0) || !isfinite(pAp)) {
-            st->status = CG_BREAKDOWN;
-            st->alpha = 0.0;
-        } else {
-            st->alpha = st->rr / pAp;
+        for (int k = 0; k < n; ++k) {
+            CgRhs &q = st->r[k];
+            q.pAp = tot[k];
+            if (q.status == CG_DONE) {
+                q.alpha = 0.0;
+            } else if (!(tot[k] > 0.0) || !isfinite(tot[k])) {
+                q.alpha = 0.0;
+                q.status = CG_BREAKDOWN;
+                st->status = CG_BREAKDOWN;
+            } else {
+                q.alpha = q.rr / tot[k];
+            }
         }
     } else if (kind == FIN_CG_RR) {
-        const double rr_new = tot[0];
         st->iter += 1;
-        st->rr_prev = st->rr;
-        st->beta = rr_new / st->rr;
-        st->rr = rr_new;
-        if (!isfinite(rr_new)) {
+        bool want = false, bad = false;
+        for (int k = 0; k < n; ++k) {
+            CgRhs &q = st->r[k];
+            if (q.status == CG_DONE) {
+                q.beta = 0.0;
+                continue;
+            }
+            const double rr_new = tot[k];
+            q.rr_prev = q.rr;
+            q.beta = rr_new / q.rr;
+            q.rr = rr_new;
+            if (!isfinite(rr_new)) bad = true;
+            if (rr_new <= q.rr_stop || (st->delta2 > 0.0 && rr_new < st->delta2 * q.rr_max)) want = true;
+            if (rr_new > q.rr_max) q.rr_max = rr_new;
+        }
+        if (bad)
             st->status = CG_BREAKDOWN;
-        } else if (rr_new <= st->rr_stop) {
-            st->status = st->delta2 > 0.0 ? CG_RELIABLE : CG_CONVERGED;
-        } else if (st->delta2 > 0.0 && rr_new < st->delta2 * st->rr_max) {
+        else if (want)
             st->status = CG_RELIABLE;
-        } else if (st->iter >= st->maxiter) {
+        else if (st->iter >= st->maxiter)
             st->status = CG_MAXITER;
-        }
-        if (rr_new > st->rr_max) st->rr_max = rr_new;
     } else if (kind == FIN_CG_TRUE) {
-        // rr_true = |rhs - A x|^2 with x the accumulated solution.
-        const double rt = tot[0];
-        st->rr_true = rt;
         st->reliable_updates += 1;
-        if (!isfinite(rt)) {
-            st->status = CG_BREAKDOWN;
-        } else if (rt <= st->rr_stop) {
-            st->status = CG_DONE;
-        } else if (st->iter >= st->maxiter) {
-            st->status = CG_MAXITER;
-        } else {
-            st->beta = rt / st->rr_prev;
-            st->rr = rt;
-            st->rr_max = rt;
-            st->status = CG_RUNNING;
+        bool all_done = true, bad = false;
+        for (int k = 0; k < n; ++k) {
+            CgRhs &q = st->r[k];
+            if (q.status == CG_DONE) {
+                q.beta = 0.0;
+                continue;
+            }
+            const double rt = tot[k];
+            q.rr_true = rt;
+            if (!isfinite(rt)) {
+                bad = true;
+            } else if (rt <= q.rr_stop) {
+                q.status = CG_DONE;
+                q.iter_done = st->iter;
+                q.beta = 0.0;
+            } else {
+                q.beta = rt / q.rr_prev;
+                q.rr = rt;
+                q.rr_max = rt;
+            }
+            all_done = all_done && q.status == CG_DONE;
         }
+        st->status = bad ? CG_BREAKDOWN
+                         : all_done ? CG_DONE : (st->iter >= st->maxiter ? CG_MAXITER : CG_RUNNING);
     }
 }
 
 // Grid-wide deterministic reduction of NV doubles per thread with the
-// last-block pattern.  All threads of the block must call it.
+// last-block pattern (one value set for the whole grid).  All threads of
+// the block must call it.
 template <int NV>
-__device__ __forceinline__ void grid_reduce(double (&v)[NV], const Reduction &red, FinalizeKind kind, CgState *st,
-                                            double *out)
+__device__ __forceinline__ void grid_reduce(double (&v)[NV], const Reduction &red, double *out)
 {
     __shared__ double smem[NV * 32];
     __shared__ bool is_last;
@@ -818,7 +862,61 @@ __device__ __forceinline__ void grid_reduce(double (&v)[NV], const Reduction &re
     }
     block_sum<NV>(s, smem);
     if (threadIdx.x == 0) {
-        cg_finalize<NV>(kind, s, st, out);
+#pragma unroll
+        for (int k = 0; k < NV; ++k) out[k] = s[k];
+        *red.counter = 0u;
+    }
+}
+
+// Grid-wide reduction segmented by right-hand side: element e of a batched
+// field belongs to rhs e & (nrhs - 1) (nrhs a power of two <= 32, the rhs
+// index fastest), so in a warp the lanes of one rhs are lane & (nrhs - 1).
+// NV values per element; the last block sums the per-block partials of each
+// (value, rhs) in block order and finalises.  All threads must call it;
+// blockDim.x must be a multiple of 32 and at most 256.
+template <int NV>
+__device__ __forceinline__ void grid_reduce_rhs(double (&v)[NV], int rhs_log2, const Reduction &red,
+                                                FinalizeKind kind, CgState *st, double *out)
+{
+    __shared__ double sw[NV][8][kMaxRhs];  // [value][warp][rhs]; blocks of <= 256 threads
+    __shared__ double tot[NV * kMaxRhs];
+    __shared__ bool is_last;
+    const int n = 1 << rhs_log2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+        for (int off = 16; off >= n; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
+    if (lane < n)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sw[k][warp][lane] = v[k];
+    __syncthreads();
+    if (threadIdx.x < NV * n) {
+        const int k = threadIdx.x / n, r = threadIdx.x % n;
+        double b = 0.0;
+        for (int w = 0; w < nw; ++w) b += sw[k][w][r];
+        red.partials[((size_t)k * n + r) * gridDim.x + blockIdx.x] = b;
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(red.counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    // one warp per (value, rhs): lane-strided sums, then a fixed shuffle tree
+    for (int q = warp; q < NV * n; q += nw) {
+        double a = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32) a += __ldcg(red.partials + (size_t)q * gridDim.x + b);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+        if (lane == 0) tot[q] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (kind == FIN_STORE) {
+            for (int q = 0; q < NV * n; ++q) out[q] = tot[q];
+        } else {
+            cg_finalize_rhs(kind, tot, st);
+        }
         *red.counter = 0u;
     }
 }
@@ -844,6 +942,8 @@ struct DslashLaunch {
     Geom g;
     int out_parity;
     int both;
+    int rhs_log2;       // batched fields: element = site * 2^rhs_log2 + rhs
+    int tpb;            // threads per block (FP32/16-bit kernels; 0: default)
     int dagger;
     GaugeView U;
     SpinorView in[2], out[2], y[2];

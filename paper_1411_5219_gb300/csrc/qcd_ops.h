@@ -12,9 +12,10 @@ void note_launches(int n = 1);
 // h sites each, in storage precision `prec`.
 struct FieldView {
     SpinorView hv[2];
-    int nh;    // 1 or 2
-    int h;     // sites per half
-    int prec;  // qcd_prec
+    int nh;        // 1 or 2
+    int h;         // elements per half: sites << rhs_log2
+    int prec;      // qcd_prec
+    int rhs_log2;  // batched field: element = site * 2^rhs_log2 + rhs
 };
 
 // out = c[chi] * in (one complex factor per chirality), e.g. A^-1 psi.
@@ -25,13 +26,13 @@ cudaError_t launch_zero(const FieldView &f, cudaStream_t s);
 // |f|^2 reduced in FP64; `fin` says what the last block does with it.
 cudaError_t launch_norm2(const FieldView &f, const Reduction &red, FinalizeKind fin, CgState *st, double *out,
                          cudaStream_t s);
-// out[0] = |a - b|^2, out[1] = |b|^2 (F64 fields).
+// Per rhs r of the batched F64 fields: out[r] = |a - b|^2, out[n + r] = |b|^2.
 cudaError_t launch_diff_norm2(const FieldView &a, const FieldView &b, const Reduction &red, double *out,
                               cudaStream_t s);
 
 // CG vector steps.  The CG state lives on the device; every kernel below
 // except cg_true_residual returns at once unless state->status is RUNNING.
-cudaError_t launch_cg_state_init(CgState *st, double tol2, double delta2, int maxiter, cudaStream_t s);
+cudaError_t launch_cg_state_init(CgState *st, int nrhs, double tol2, double delta2, int maxiter, cudaStream_t s);
 // r = rhs (cast), p = r, x = 0, xs = 0 (if given); rr = |rhs|^2; status.
 cudaError_t launch_cg_setup(const FieldView &rhs, const FieldView &r, const FieldView &p, const FieldView &x,
                             const FieldView *xs, const Reduction &red, CgState *st, cudaStream_t s);
@@ -50,6 +51,10 @@ cudaError_t launch_cg_true_residual(const FieldView &rhs, const FieldView &q, co
 // Graph control kernels (cudaGraphSetConditional on the loop / reliable-update handles).
 cudaError_t launch_cg_ctrl_reliable(const CgState *st, cudaGraphConditionalHandle h, cudaStream_t s);
 cudaError_t launch_cg_ctrl_loop(CgState *st, cudaGraphConditionalHandle h, cudaStream_t s);
+
+// Copy between one rhs of a batched field and a plain field of the same
+// precision and halves: to_batch = 1 copies plain -> batched[rhs].
+cudaError_t launch_batch_copy(const FieldView &batched, const FieldView &plain, int rhs, int to_batch, cudaStream_t s);
 
 // Layout conversion between the host AoS form (FP64, lexicographic) and the
 // device SoA form.

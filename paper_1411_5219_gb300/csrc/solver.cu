@@ -23,6 +23,7 @@
 #include <cmath>
 #include <algorithm>
 #include <cstdio>
+#include <cstring>
 #include <vector>
 
 #include "qcd_handles.h"
@@ -34,6 +35,7 @@ struct OpCtx {
     const qcd_lattice *lat;
     double kappa, a;  // a = 2 kappa mu
     bool eo;
+    const Reduction *red;  // scratch of the fused |Mhat p|^2 reduction
 };
 
 // out = Mhat^dag Mhat in (eo) or M^dag M in (full).  t (odd half) and s
@@ -68,6 +70,7 @@ cudaError_t apply_normal(const OpCtx &c, const GaugeView &U, int recon, const Fi
         h2.cy = coef_twist(c.a);
         h2.cd = coef_real(-c.kappa * c.kappa);
         h2.reduce = reduce_alpha;
+        h2.red = c.red;
         if ((e = hop(c.lat, U, recon, h2, st)) != cudaSuccess) return e;
         // t = A^-dag D_oe^dag s
         HopArgs h3 = h;
@@ -97,6 +100,7 @@ cudaError_t apply_normal(const OpCtx &c, const GaugeView &U, int recon, const Fi
     h.cy = coef_twist(c.a);
     h.cd = coef_real(-c.kappa);
     h.reduce = reduce_alpha;
+    h.red = c.red;
     if ((e = hop(c.lat, U, recon, h, st)) != cudaSuccess) return e;
     // out = M^dag s
     HopArgs h2 = h;
@@ -176,10 +180,23 @@ cudaError_t read_state(const qcd_lattice *lat, cudaStream_t s)
 // next reliable update (mixed) or the target residual.
 cudaError_t cg_eager(const qcd_lattice *lat, const CgFields &f, cudaStream_t s)
 {
+    // the slowest running right-hand side sets the pace: its log distance to
+    // the target (and to the next reliable update) in residual^2
+    auto distance = [](const CgState &st) {
+        double d = 0.0;
+        for (int k = 0; k < st.nrhs; ++k) {
+            const CgRhs &q = st.r[k];
+            if (q.status != CG_RUNNING || q.rr <= 0.0) continue;
+            double dk = std::log(q.rr / q.rr_stop);
+            if (st.delta2 > 0.0) dk = std::min(dk, std::log(q.rr / (st.delta2 * q.rr_max)));
+            d = std::max(d, dk);
+        }
+        return d;
+    };
     cudaError_t e = read_state(lat, s);
     if (e != cudaSuccess) return e;
     int batch = 2;
-    double last_rr = lat->state_host->rr;
+    double last_d = distance(*lat->state_host);
     int last_iter = 0;
     for (;;) {
         const int status = lat->state_host->status;
@@ -191,15 +208,14 @@ cudaError_t cg_eager(const qcd_lattice *lat, const CgFields &f, cudaStream_t s)
         if ((e = read_state(lat, s)) != cudaSuccess) return e;
         const CgState &hs = *lat->state_host;
         const int done = hs.iter - last_iter;
-        if (done > 0 && hs.rr > 0.0 && last_rr > hs.rr && hs.status == CG_RUNNING) {
-            const double rate = std::log(last_rr / hs.rr) / done;
-            double rem = std::log(hs.rr / hs.rr_stop) / rate;
-            if (hs.delta2 > 0.0) rem = std::min(rem, std::log(hs.rr / (hs.delta2 * hs.rr_max)) / rate);
-            batch = (int)std::min(64.0, std::max(1.0, std::ceil(rem)));
+        const double d = distance(hs);
+        if (done > 0 && hs.status == CG_RUNNING && last_d > d && d > 0.0) {
+            const double rate = (last_d - d) / done;
+            batch = (int)std::min(64.0, std::max(1.0, std::ceil(d / rate)));
         } else {
             batch = std::max(1, std::min(8, batch));
         }
-        last_rr = hs.rr;
+        last_d = d;
         last_iter = hs.iter;
     }
 }
@@ -217,6 +233,8 @@ qcd_status cg_graph(const qcd_lattice *lat, const CgFields &f, cudaGraphExec_t *
              f.xh.hv[0].data, f.xh.hv[1].data, f.rh.hv[0].data, f.qh.hv[0].data, f.th.hv[0].data, f.sh.hv[0].data,
              f.rs.hv[0].data, f.ps.hv[0].data, f.qs.hv[0].data, f.ts.hv[0].data, f.ss.hv[0].data, f.xs.hv[0].data,
              (void *)f.state, f.rs.prec, f.rhs.nh);
+    const size_t used = strlen(key);
+    snprintf(key + used, sizeof(key) - used, "|%p|%d", (void *)f.red.partials, f.rs.rhs_log2);
     auto it = lat->graphs.find(key);
     if (it != lat->graphs.end()) {
         it->second.last_use = ++lat->graph_clock;
@@ -312,17 +330,33 @@ using namespace qcd;
         if (e_ != cudaSuccess) return check_cuda(e_, what);   \
     } while (0)
 
-extern "C" qcd_status qcd_solve_cg(const qcd_gauge *g, qcd_spinor *x, const qcd_spinor *b,
-                                   const qcd_solver_params *prm, qcd_solver_stats *stats, void *stream)
+namespace {
+
+FieldView half_of(const FieldView &f, int k)
+{
+    FieldView v = f;
+    v.nh = 1;
+    v.hv[0] = v.hv[1] = f.hv[k];
+    return v;
+}
+
+// The solve for nrhs right-hand sides in one batched CG (nrhs = 1: the
+// caller's fields are used in place).
+qcd_status solve_impl(const qcd_gauge *g, qcd_spinor *const *x, const qcd_spinor *const *b, int nrhs,
+                      const qcd_solver_params *prm, qcd_solver_stats *stats, cudaStream_t s)
 {
     const auto t0 = std::chrono::steady_clock::now();
     if (!g || !x || !b || !prm) return fail(QCD_ERR_INVALID_ARG, "solve_cg: NULL argument");
+    if (nrhs < 1 || nrhs > kMaxRhs) return fail(QCD_ERR_INVALID_ARG, "solve_cg: nrhs = %d not in 1..%d", nrhs, kMaxRhs);
     const qcd_lattice *lat = g->lat;
-    if (x->lat != lat || b->lat != lat) return fail(QCD_ERR_INVALID_ARG, "solve_cg: lattices differ");
-    if (x->parity != QCD_PARITY_FULL || b->parity != QCD_PARITY_FULL || x->prec != QCD_PREC_F64 ||
-        b->prec != QCD_PREC_F64)
-        return fail(QCD_ERR_INVALID_ARG, "solve_cg: x and b must be FULL F64 fields");
-    if (x == b || x->data == b->data) return fail(QCD_ERR_INVALID_ARG, "solve_cg: x aliases b");
+    for (int k = 0; k < nrhs; ++k) {
+        if (!x[k] || !b[k]) return fail(QCD_ERR_INVALID_ARG, "solve_cg: NULL field");
+        if (x[k]->lat != lat || b[k]->lat != lat) return fail(QCD_ERR_INVALID_ARG, "solve_cg: lattices differ");
+        if (x[k]->parity != QCD_PARITY_FULL || b[k]->parity != QCD_PARITY_FULL || x[k]->prec != QCD_PREC_F64 ||
+            b[k]->prec != QCD_PREC_F64)
+            return fail(QCD_ERR_INVALID_ARG, "solve_cg: x and b must be FULL F64 fields");
+        if (x[k]->data == b[k]->data) return fail(QCD_ERR_INVALID_ARG, "solve_cg: x aliases b");
+    }
     if (g->prec != QCD_PREC_F64) return fail(QCD_ERR_INVALID_ARG, "solve_cg: the gauge field must be F64");
     if (!(prm->tol > 0.0) || prm->maxiter < 1 || !std::isfinite(prm->kappa) || !std::isfinite(prm->mu))
         return fail(QCD_ERR_INVALID_ARG, "solve_cg: bad tol/maxiter/kappa/mu");
@@ -335,7 +369,6 @@ extern "C" qcd_status qcd_solve_cg(const qcd_gauge *g, qcd_spinor *x, const qcd_
     if (mixed && !(prm->reliable_delta > 0.0 && prm->reliable_delta < 1.0))
         return fail(QCD_ERR_INVALID_ARG, "solve_cg: reliable_delta must be in (0, 1)");
 
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int sp = prm->inner_prec;
     // DF64 links are kept at 18 reals (rebuilding a row in double-float
     // arithmetic costs more than the bytes it saves)
@@ -346,30 +379,54 @@ extern "C" qcd_status qcd_solve_cg(const qcd_gauge *g, qcd_spinor *x, const qcd_
     const GaugeView Us = mixed ? gauge_view(g, sp, srecon, s, &st) : Uh;
     if (st != QCD_OK) return st;
 
-    OpCtx c{lat, prm->kappa, 2.0 * prm->kappa * prm->mu, prm->eo != 0};
+    int L = 0;
+    while ((1 << L) < nrhs) ++L;
+    const int N = 1 << L;
+    OpCtx c{lat, prm->kappa, 2.0 * prm->kappa * prm->mu, prm->eo != 0, nullptr};
     const bool tw = c.a != 0.0;
     const int nh = c.eo ? 1 : 2;
-    const FieldView bf = view_of(b), xf = view_of(x);
+
+    // b and x as (batched) full fields
+    FieldView bf, xf;
+    if (N == 1) {
+        bf = view_of(b[0]);
+        xf = view_of(x[0]);
+    } else {
+        bf = ws_field(lat, "cg_bb", 2, QCD_PREC_F64, L);
+        xf = ws_field(lat, "cg_xx", 2, QCD_PREC_F64, L);
+        if (!bf.hv[0].data || !xf.hv[0].data) return fail(QCD_ERR_OOM, "solve_cg: workspace");
+        QCD_TRY(launch_zero(bf, s), "solve_cg: gather");  // padding right-hand sides are zero (solved at once)
+        for (int k = 0; k < nrhs; ++k) QCD_TRY(launch_batch_copy(bf, view_of(b[k]), k, 1, s), "solve_cg: gather");
+    }
+    // reduction scratch: NV (<= 2) x N partials per block of the largest grid
+    Reduction red = reduction_of(lat);
+    if (N > 1) {
+        const size_t need = 2 * (size_t)N * (((size_t)2 * (lat->h << L) + 63) / 64 + 64);
+        red.partials = static_cast<double *>(workspace(lat, "cg_partials", need * sizeof(double)));
+        red.cap = need;
+        if (!red.partials) return fail(QCD_ERR_OOM, "solve_cg: workspace");
+    }
+    c.red = &red;
 
     // FP64 fields
-    FieldView rhs = c.eo ? ws_field(lat, "cg_rhs", 1, QCD_PREC_F64) : bf;
-    const FieldView xh = c.eo ? view_half(x, 0) : xf;
-    const FieldView rh = ws_field(lat, "cg_r", nh, QCD_PREC_F64);
-    const FieldView ph = ws_field(lat, "cg_p", nh, QCD_PREC_F64);
-    const FieldView qh = ws_field(lat, "cg_q", nh, QCD_PREC_F64);
-    const FieldView th = ws_field(lat, "cg_t", 1, QCD_PREC_F64);
-    const FieldView sh = ws_field(lat, "cg_s", nh, QCD_PREC_F64);
+    FieldView rhs = c.eo ? ws_field(lat, "cg_rhs", 1, QCD_PREC_F64, L) : bf;
+    const FieldView xh = c.eo ? half_of(xf, 0) : xf;
+    const FieldView rh = ws_field(lat, "cg_r", nh, QCD_PREC_F64, L);
+    const FieldView ph = ws_field(lat, "cg_p", nh, QCD_PREC_F64, L);
+    const FieldView qh = ws_field(lat, "cg_q", nh, QCD_PREC_F64, L);
+    const FieldView th = ws_field(lat, "cg_t", 1, QCD_PREC_F64, L);
+    const FieldView sh = ws_field(lat, "cg_s", nh, QCD_PREC_F64, L);
     if (!rhs.hv[0].data || !rh.hv[0].data || !ph.hv[0].data || !qh.hv[0].data || !th.hv[0].data || !sh.hv[0].data)
         return fail(QCD_ERR_OOM, "solve_cg: workspace");
     // inner fields
     FieldView rs = rh, ps = ph, qs = qh, ts = th, ss = sh, xs = xh;
     if (mixed) {
-        rs = ws_field(lat, "cg_rs", nh, sp);
-        ps = ws_field(lat, "cg_ps", nh, sp);
-        qs = ws_field(lat, "cg_qs", nh, sp);
-        ts = ws_field(lat, "cg_ts", 1, sp);
-        ss = ws_field(lat, "cg_ss", nh, sp);
-        xs = ws_field(lat, "cg_xs", nh, sp == QCD_PREC_DF64 ? QCD_PREC_DF64 : QCD_PREC_F32);
+        rs = ws_field(lat, "cg_rs", nh, sp, L);
+        ps = ws_field(lat, "cg_ps", nh, sp, L);
+        qs = ws_field(lat, "cg_qs", nh, sp, L);
+        ts = ws_field(lat, "cg_ts", 1, sp, L);
+        ss = ws_field(lat, "cg_ss", nh, sp, L);
+        xs = ws_field(lat, "cg_xs", nh, sp == QCD_PREC_DF64 ? QCD_PREC_DF64 : QCD_PREC_F32, L);
         if (!rs.hv[0].data || !ps.hv[0].data || !qs.hv[0].data || !ts.hv[0].data || !ss.hv[0].data ||
             !xs.hv[0].data)
             return fail(QCD_ERR_OOM, "solve_cg: workspace");
@@ -377,8 +434,8 @@ extern "C" qcd_status qcd_solve_cg(const qcd_gauge *g, qcd_spinor *x, const qcd_
 
     // ---- right-hand side of the CG system
     if (c.eo) {
-        const FieldView be = view_half(b, 0), bo = view_half(b, 1);
-        const FieldView bp = ws_field(lat, "cg_bp", 1, QCD_PREC_F64);
+        const FieldView be = half_of(bf, 0), bo = half_of(bf, 1);
+        const FieldView bp = ws_field(lat, "cg_bp", 1, QCD_PREC_F64, L);
         if (!bp.hv[0].data) return fail(QCD_ERR_OOM, "solve_cg: workspace");
         const FieldView *src = &bo;
         if (tw) {  // th = A^-1 b_o
@@ -417,21 +474,21 @@ extern "C" qcd_status qcd_solve_cg(const qcd_gauge *g, qcd_spinor *x, const qcd_
         h4.cd = coef_real(-c.kappa * c.kappa);
         QCD_TRY(hop(lat, Uh, g->recon, h4, s), "solve_cg: source");
     } else if (!prm->normal) {
-        rhs = ws_field(lat, "cg_rhs", 2, QCD_PREC_F64);
+        rhs = ws_field(lat, "cg_rhs", 2, QCD_PREC_F64, L);
         if (!rhs.hv[0].data) return fail(QCD_ERR_OOM, "solve_cg: workspace");
         QCD_TRY(apply_full_m(c, Uh, g->recon, bf, rhs, 1, s), "solve_cg: source");
     }
 
     // ---- CG
-    CgFields F{c, Uh, Us, g->recon, srecon, mixed, rhs, xh, rh, qh, th, sh, rs, ps, qs, ts, ss, xs,
-               reduction_of(lat), lat->state};
+    CgFields F{c, Uh, Us, g->recon, srecon, mixed, rhs, xh, rh, qh, th, sh, rs, ps, qs, ts, ss, xs, red, lat->state};
     const double delta = mixed ? prm->reliable_delta : 0.0;
-    QCD_TRY(launch_cg_state_init(lat->state, prm->tol * prm->tol, delta * delta, prm->maxiter, s), "solve_cg: init");
+    QCD_TRY(launch_cg_state_init(lat->state, N, prm->tol * prm->tol, delta * delta, prm->maxiter, s), "solve_cg: init");
     QCD_TRY(launch_cg_setup(rhs, rs, ps, xh, mixed ? &xs : nullptr, F.red, lat->state, s), "solve_cg: setup");
 
     qcd_status result = QCD_OK;
-    const bool use_graph = !profiling_active();
-    if (use_graph) {
+    if (!profiling_active()) {
+        // choose the inner kernels' launch shape before it is frozen in the graph
+        tuned_tpb(lat, Us, sp, srecon, L, !c.eo, s);
         cudaGraphExec_t exec = nullptr;
         qcd_status gst = cg_graph(lat, F, &exec);
         if (gst != QCD_OK) return gst;
@@ -444,20 +501,16 @@ extern "C" qcd_status qcd_solve_cg(const qcd_gauge *g, qcd_spinor *x, const qcd_
     } else {
         QCD_TRY(cg_eager(lat, F, s), "solve_cg: iterations");
     }
-    {
-        const int status = lat->state_host->status;
-        if (status == CG_BREAKDOWN)
-            result = fail(QCD_ERR_BREAKDOWN, "solve_cg: breakdown (non-positive <p,Ap> or non-finite values)");
-        else if (status != CG_DONE)
-            result = fail(QCD_ERR_NOT_CONVERGED, "solve_cg: maxiter reached");
-    }
+    const CgState hs = *lat->state_host;
+    if (hs.status == CG_BREAKDOWN)
+        result = fail(QCD_ERR_BREAKDOWN, "solve_cg: breakdown (non-positive <p,Ap> or non-finite values)");
+    else if (hs.status != CG_DONE)
+        result = fail(QCD_ERR_NOT_CONVERGED, "solve_cg: maxiter reached");
     if (mixed && result != QCD_OK) QCD_TRY(launch_cg_accum_x(xh, xs, s), "solve_cg: accumulate");
 
     // ---- odd sites and residuals
-    const CgState hs = *lat->state_host;
-    double true_rel = std::sqrt(hs.b2 > 0 ? hs.rr_true / hs.b2 : 0.0);
     if (c.eo) {
-        const FieldView xo = view_half(x, 1), bo = view_half(b, 1);
+        const FieldView xo = half_of(xf, 1), bo = half_of(bf, 1);
         HopArgs h{};  // x_o = A^-1 b_o + kappa A^-1 D_oe x_e
         h.fin = FIN_STORE;
         h.out = &xo;
@@ -469,37 +522,63 @@ extern "C" qcd_status qcd_solve_cg(const qcd_gauge *g, qcd_spinor *x, const qcd_
         h.cd = coef_scale(coef_twist_inv(c.a), c.kappa);
         QCD_TRY(hop(lat, Uh, g->recon, h, s), "solve_cg: reconstruct");
     }
+    double true_rel[kMaxRhs], full_rel[kMaxRhs];
+    for (int k = 0; k < N; ++k) true_rel[k] = hs.r[k].b2 > 0 ? std::sqrt(hs.r[k].rr_true / hs.r[k].b2) : 0.0;
+    std::vector<double> r2(2 * N);
     if (hs.status != CG_DONE) {  // true residual of the CG system, for the stats
         QCD_TRY(apply_normal(c, Uh, g->recon, xh, qh, th, sh, false, false, s), "solve_cg: residual");
-        QCD_TRY(launch_diff_norm2(qh, rhs, F.red, lat->red_out, s), "solve_cg: residual");
-        double r2[2];
-        QCD_TRY(cudaMemcpyAsync(r2, lat->red_out, sizeof(r2), cudaMemcpyDeviceToHost, s), "solve_cg: residual");
+        QCD_TRY(launch_diff_norm2(qh, rhs, F.red, lat->red_out_big, s), "solve_cg: residual");
+        QCD_TRY(cudaMemcpyAsync(r2.data(), lat->red_out_big, 2 * N * sizeof(double), cudaMemcpyDeviceToHost, s),
+                "solve_cg: residual");
         QCD_TRY(cudaStreamSynchronize(s), "solve_cg: residual");
-        true_rel = r2[1] > 0 ? std::sqrt(r2[0] / r2[1]) : 0.0;
+        for (int k = 0; k < N; ++k) true_rel[k] = r2[N + k] > 0 ? std::sqrt(r2[k] / r2[N + k]) : 0.0;
     }
     // full-system residual |b - M x| / |b|  (normal: |b - M^dag M x| / |b|)
-    const FieldView mx = ws_field(lat, "cg_full", 2, QCD_PREC_F64);
+    const FieldView mx = ws_field(lat, "cg_full", 2, QCD_PREC_F64, L);
     if (!mx.hv[0].data) return fail(QCD_ERR_OOM, "solve_cg: workspace");
     QCD_TRY(apply_full_m(c, Uh, g->recon, xf, mx, 0, s), "solve_cg: residual");
     const FieldView *chk = &mx;
     FieldView mx2;
     if (!c.eo && prm->normal) {
-        mx2 = ws_field(lat, "cg_full2", 2, QCD_PREC_F64);
+        mx2 = ws_field(lat, "cg_full2", 2, QCD_PREC_F64, L);
         if (!mx2.hv[0].data) return fail(QCD_ERR_OOM, "solve_cg: workspace");
         QCD_TRY(apply_full_m(c, Uh, g->recon, mx, mx2, 1, s), "solve_cg: residual");
         chk = &mx2;
     }
-    QCD_TRY(launch_diff_norm2(*chk, bf, F.red, lat->red_out, s), "solve_cg: residual");
-    double r2[2];
-    QCD_TRY(cudaMemcpyAsync(r2, lat->red_out, sizeof(r2), cudaMemcpyDeviceToHost, s), "solve_cg: residual");
+    QCD_TRY(launch_diff_norm2(*chk, bf, F.red, lat->red_out_big, s), "solve_cg: residual");
+    QCD_TRY(cudaMemcpyAsync(r2.data(), lat->red_out_big, 2 * N * sizeof(double), cudaMemcpyDeviceToHost, s),
+            "solve_cg: residual");
+    if (N > 1)
+        for (int k = 0; k < nrhs; ++k) QCD_TRY(launch_batch_copy(xf, view_of(x[k]), k, 0, s), "solve_cg: scatter");
     QCD_TRY(cudaStreamSynchronize(s), "solve_cg: residual");
+    for (int k = 0; k < N; ++k) full_rel[k] = r2[N + k] > 0 ? std::sqrt(r2[k] / r2[N + k]) : 0.0;
 
     if (stats) {
-        stats->iterations = hs.iter;
-        stats->reliable_updates = hs.reliable_updates;
-        stats->true_rel_residual = true_rel;
-        stats->full_rel_residual = r2[1] > 0 ? std::sqrt(r2[0] / r2[1]) : 0.0;
-        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        for (int k = 0; k < nrhs; ++k) {
+            stats[k].iterations = hs.r[k].status == CG_DONE ? hs.r[k].iter_done : hs.iter;
+            stats[k].reliable_updates = hs.reliable_updates;
+            stats[k].true_rel_residual = true_rel[k];
+            stats[k].full_rel_residual = full_rel[k];
+            stats[k].seconds = secs;
+        }
     }
     return result;
+}
+
+}  // namespace
+
+extern "C" qcd_status qcd_solve_cg(const qcd_gauge *g, qcd_spinor *x, const qcd_spinor *b,
+                                   const qcd_solver_params *prm, qcd_solver_stats *stats, void *stream)
+{
+    qcd_spinor *xs[1] = {x};
+    const qcd_spinor *bs[1] = {b};
+    return solve_impl(g, xs, bs, 1, prm, stats, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" qcd_status qcd_solve_cg_multi(const qcd_gauge *g, qcd_spinor *const *x, const qcd_spinor *const *b,
+                                         int nrhs, const qcd_solver_params *prm, qcd_solver_stats *stats,
+                                         void *stream)
+{
+    return solve_impl(g, x, b, nrhs, prm, stats, static_cast<cudaStream_t>(stream));
 }

@@ -74,6 +74,9 @@ _SIGS = {
     "qcd_profile_end": (_i, [ctypes.POINTER(Profile)]),
     "qcd_kernel_launches": (ctypes.c_ulonglong, []),
     "qcd_norm2_noalloc": (_i, [_p, ctypes.c_size_t, _p, _p]),
+    "qcd_apply_dslash_multi": (_i, [_p, ctypes.POINTER(_p), ctypes.POINTER(_p), _i, _i, _p]),
+    "qcd_solve_cg_multi": (_i, [_p, ctypes.POINTER(_p), ctypes.POINTER(_p), _i, ctypes.POINTER(SolverParams),
+                                ctypes.POINTER(SolverStats), _p]),
 }
 
 _lib = None
@@ -275,6 +278,35 @@ def apply_M(gauge: Gauge, out: Spinor, inp: Spinor, kappa: float, mu: float = 0.
     """out = M inp (full) or Mhat inp (even-odd); see qcd_apply_M."""
     _check(lib().qcd_apply_M(gauge.handle, out.handle, inp.handle, float(kappa), float(mu), int(bool(eo)),
                              int(bool(dagger)), _stream(stream)), "qcd_apply_M")
+
+
+def _handles(fields):
+    return (_p * len(fields))(*[f.handle.value for f in fields])
+
+
+def apply_dslash_multi(gauge: Gauge, outs, ins, dagger: bool = False, stream=None):
+    """outs[k] = D_hop ins[k] for all k in one batched launch (qcd_apply_dslash_multi)."""
+    if len(outs) != len(ins):
+        raise ValueError("outs and ins differ in length")
+    _check(lib().qcd_apply_dslash_multi(gauge.handle, _handles(outs), _handles(ins), len(ins), int(bool(dagger)),
+                                        _stream(stream)), "qcd_apply_dslash_multi")
+
+
+def solve_cg_multi(gauge: Gauge, xs, bs, kappa: float, mu: float = 0.0, tol: float = 1e-10, maxiter: int = 20000,
+                   eo: bool = True, normal: bool = False, inner_prec: str = "f64", inner_recon: int = 12,
+                   reliable_delta: float = 0.1, stream=None, raise_on_error: bool = True):
+    """Batched CG over len(bs) systems (qcd_solve_cg_multi); returns (status, [stats dict])."""
+    if len(xs) != len(bs):
+        raise ValueError("xs and bs differ in length")
+    n = len(bs)
+    prm = SolverParams(float(kappa), float(mu), float(tol), int(maxiter), int(bool(eo)), int(bool(normal)),
+                       PREC[inner_prec], int(inner_recon), float(reliable_delta))
+    st = (SolverStats * n)()
+    status = lib().qcd_solve_cg_multi(gauge.handle, _handles(xs), _handles(bs), n, ctypes.byref(prm), st,
+                                      _stream(stream))
+    if raise_on_error and status != 0:
+        _check(status, "qcd_solve_cg_multi")
+    return status, [{k: getattr(st[i], k) for k, _ in SolverStats._fields_} for i in range(n)]
 
 
 def solve_cg(gauge: Gauge, x: Spinor, b: Spinor, kappa: float, mu: float = 0.0, tol: float = 1e-10,

@@ -460,3 +460,99 @@ def test_df64_recon12_rejected(q):
     si, so = q.Spinor(lat, "odd", "df64"), q.Spinor(lat, "even", "df64")
     with pytest.raises(q.QcdError):
         q.apply_dslash(g, so, si)
+
+
+# ------------------------------------------------------ batched multi-RHS
+
+def sources_12_point_4_gauss(dims, seed):
+    srcs = [syn.point_source(dims, s_, c_) for s_ in range(4) for c_ in range(3)]
+    srcs += [syn.gaussian_spinor(dims, seed + k) for k in range(4)]
+    return srcs
+
+
+@pytest.mark.parametrize("prec,recon", [("f64", 18), ("f32", 12), ("f16", 12), ("df64", 18)])
+@pytest.mark.parametrize("nrhs", [16, 3])
+def test_dslash_multi_matches_oracle(q, prec, recon, nrhs):
+    dims = (8, 6, 4, 10)
+    lat, U, g = gauge(q, dims, recon=recon)
+    srcs = sources_12_point_4_gauss(dims, 40)[:nrhs]
+    for dagger in (False, True):
+        ins, outs = [], []
+        for k, psi in enumerate(srcs):
+            si = q.Spinor(lat, "odd", prec)
+            si.upload(syn.to_half(psi, 1))
+            ins.append(si)
+            outs.append(q.Spinor(lat, "even", prec))
+        q.apply_dslash_multi(g, outs, ins, dagger=dagger)
+        for k, psi in enumerate(srcs):
+            want = oracle.dhop_eo(U, syn.to_half(psi, 1), 0, dagger=dagger)
+            if not np.any(want):
+                continue
+            assert F.rel_err(outs[k].download(), want) <= tol_of(prec if prec != "df64" else "f64"), (k, prec)
+
+
+@pytest.mark.parametrize("inner", ["f64", "f32", "f16"])
+def test_solve_multi_12_point_4_gauss(q, inner):
+    """16 sources (one point source per spin-colour + 4 Gaussian) in one
+    batched CG; each solution matches its single-RHS solve and meets 1e-10."""
+    dims = (8, 8, 8, 4)
+    kappa, mu = 0.155, 0.0
+    lat, U, g = gauge(q, dims, eps=0.2, seed=77)
+    srcs = sources_12_point_4_gauss(dims, 50)
+    bs, xs = [], []
+    for psi in srcs:
+        b = q.Spinor(lat, "full", "f64")
+        b.upload(psi)
+        bs.append(b)
+        xs.append(q.Spinor(lat, "full", "f64"))
+    status, stats = q.solve_cg_multi(g, xs, bs, kappa, mu, tol=1e-10, inner_prec=inner)
+    assert status == 0
+    for k, psi in enumerate(srcs):
+        assert stats[k]["true_rel_residual"] <= 1e-10, (k, stats[k])
+        x1 = q.Spinor(lat, "full", "f64")
+        st1, s1 = q.solve_cg(g, x1, bs[k], kappa, mu, tol=1e-10, inner_prec=inner)
+        xb = xs[k].download()
+        assert F.rel_err(xb, x1.download()) <= 1e-8
+        if k in (0, 7, 12, 15):
+            assert schur_residual_oracle(U, psi, xb, kappa, mu) <= 1.5e-10
+
+
+def test_solve_multi_padding_and_zero(q):
+    """3 systems (padded to 4) including a zero source: that one is solved at once."""
+    dims = (4, 4, 4, 8)
+    lat, U, g = gauge(q, dims, eps=0.2, seed=90)
+    srcs = [syn.gaussian_spinor(dims, 91), np.zeros((8, 4, 4, 4, 4, 3), dtype=complex), syn.gaussian_spinor(dims, 92)]
+    bs, xs = [], []
+    for psi in srcs:
+        b = q.Spinor(lat, "full", "f64")
+        b.upload(psi)
+        bs.append(b)
+        xs.append(q.Spinor(lat, "full", "f64"))
+    status, stats = q.solve_cg_multi(g, xs, bs, 0.15, 0.02, tol=1e-10)
+    assert status == 0
+    assert np.all(xs[1].download() == 0) and stats[1]["iterations"] == 0
+    for k in (0, 2):
+        xo, _ = oracle.solve_eo(U, srcs[k], 0.15, 0.02, tol=1e-12)
+        assert F.rel_err(xs[k].download(), xo) <= 1e-7
+
+
+def test_autotuner_file_cache(tmp_path):
+    """The block-size autotuner writes its choice to QCD_TUNE_CACHE; a second
+    process reads it back instead of timing again."""
+    import os
+    import subprocess
+    import sys
+    cache = tmp_path / "tune.txt"
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "from paper_1411_5219_gb300 import qcd, synthetic as syn\n"
+        "lat = qcd.Lattice((8, 8, 8, 4), -1); g = qcd.Gauge(lat, 'f64', 12); g.upload(syn.gauge_field((8, 8, 8, 4), 0.2, 1))\n"
+        "a, b = qcd.Spinor(lat, 'odd', 'f32'), qcd.Spinor(lat, 'even', 'f32')\n"
+        "qcd.apply_dslash(g, b, a); qcd.stream_sync()\n"
+    ) % os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, QCD_TUNE_CACHE=str(cache))
+    subprocess.run([sys.executable, "-c", code], check=True, env=env)
+    lines = cache.read_text().split()
+    assert len(lines) == 2 and lines[0].startswith("dslash:p1:r12:n0:b0:8x8x8x4") and lines[1] in ("64", "128", "256")
+    subprocess.run([sys.executable, "-c", code], check=True, env=env)
+    assert cache.read_text().split() == lines
