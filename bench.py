@@ -281,6 +281,79 @@ def batched_block(qcd, torch, flush, hbm, reps):
     return res
 
 
+def serving_block(qcd, torch, n_requests=2000, rate=60.0, slots=8, seed=1006):
+    """configs[4]: a Poisson stream of even-odd solves of five volumes, kappa
+    uniform in [0.12, 0.16], 3 resident gauge fields per volume, FP16-mixed
+    CG to 1e-10, admitted by slot and device-memory budget."""
+    import threading
+    from paper_1411_5219_gb300 import synthetic as syn
+    rng = np.random.default_rng(seed)
+    vols = syn.SWEEP_VOLUMES
+    t_setup = time.time()
+    fields, gids, pools = [], {}, {}
+    sv = qcd.Server(slots=slots, memory_budget=64 << 30)
+    for vi, dims in enumerate(vols):
+        lat = qcd.Lattice(dims, -1)
+        for k in range(3):
+            g = qcd.Gauge(lat, "f64", 18)
+            g.upload(syn.gauge_field(dims, 0.2, seed + 10 * vi + k, device="cuda"))
+            g.prepare("f16", 12)
+            fields.append((lat, g))
+            gids[(vi, k)] = sv.add_gauge(g)
+        pools[vi] = [syn.gaussian_spinor(dims, seed + 100 * vi + j) for j in range(2)]
+    torch.cuda.synchronize()
+    t_setup = time.time() - t_setup
+    # warm each volume once (graph capture, tuning) before the stream
+    warm = []
+    for vi in range(len(vols)):
+        b = pools[vi][0]
+        x = np.empty_like(b)
+        warm.append(sv.submit(gids[(vi, 0)], b, x, 0.14, inner_prec="f16"))
+    for i in warm:
+        sv.wait(i)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_requests))
+    picks = [(int(rng.integers(len(vols))), int(rng.integers(3)), float(rng.uniform(0.12, 0.16)))
+             for _ in range(n_requests)]
+    results, ids = [None] * n_requests, [None] * n_requests
+    ready = threading.Semaphore(0)
+
+    def waiter():
+        for k in range(n_requests):
+            ready.acquire()
+            results[k] = sv.wait(ids[k])
+
+    th = threading.Thread(target=waiter)
+    th.start()
+    t0 = time.time()
+    for k, (vi, gk, kappa) in enumerate(picks):
+        dt = arrivals[k] - (time.time() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        b = pools[vi][k % 2]
+        ids[k] = sv.submit(gids[(vi, gk)], b, np.empty_like(b), kappa, inner_prec="f16")
+        ready.release()
+    th.join()
+    wall = time.time() - t0
+    lat_s = np.array([r["t_end"] - r["t_submit"] for r in results])
+    queue_s = np.array([r["t_start"] - r["t_submit"] for r in results])
+    span = max(r["t_end"] for r in results) - min(r["t_submit"] for r in results)
+    per_vol = {}
+    for (vi, _, _), r in zip(picks, results):
+        d = per_vol.setdefault("x".join(map(str, vols[vi])), [])
+        d.append(r["t_end"] - r["t_start"])
+    out = {"requests": n_requests, "arrival_rate_per_s": rate, "slots": slots, "memory_budget_GiB": 64,
+           "solves_s": n_requests / span, "wall_s": wall, "setup_s": t_setup,
+           "latency_p50_ms": float(np.percentile(lat_s, 50) * 1e3),
+           "latency_p99_ms": float(np.percentile(lat_s, 99) * 1e3),
+           "queue_p50_ms": float(np.percentile(queue_s, 50) * 1e3),
+           "queue_p99_ms": float(np.percentile(queue_s, 99) * 1e3),
+           "service_ms_median_by_volume": {k: float(np.median(v) * 1e3) for k, v in per_vol.items()},
+           "all_ok": all(r["status"] == 0 for r in results),
+           "max_true_rel_residual": max(r["stats"]["true_rel_residual"] for r in results)}
+    sv.close()
+    return out
+
+
 def cpu_oracle_sample(target_s=15.0):
     """Time FP64 oracle CG iterations on this host's cores (bounded sample)."""
     import oracle
@@ -370,6 +443,7 @@ def main():
     ap.add_argument("--dslash", nargs=3, metavar=("DIMS", "PREC", "RECON"),
                     help="only launch the even-odd Dslash (e.g. 48x48x48x12 f16 12), for profilers")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--serve-requests", type=int, default=2000)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -509,6 +583,7 @@ def main():
         t4 = timed_steps(torch, lambda: p4.solve(qcd, eo=False, normal=True), args.steps, flush)
         line["full_4x4_normal_solves_s"] = args.steps / float(np.sum(t4))
         del p4
+        line["serving"] = serving_block(qcd, torch, n_requests=args.serve_requests)
         line["dslash_sweep"] = dslash_sweep(qcd, torch, flush, hbm)
         line["dslash_sweep_note"] = (f"cold L2 (flushed before each launch); GB/s on compulsory bytes per "
                                      f"output site; frac of {hbm_kind} HBM {hbm} GB/s")

@@ -248,6 +248,58 @@ qcd_status qcd_solve_cg(const qcd_gauge *g, qcd_spinor *x, const qcd_spinor *b, 
 qcd_status qcd_solve_cg_multi(const qcd_gauge *g, qcd_spinor *const *x, const qcd_spinor *const *b, int nrhs,
                               const qcd_solver_params *params, qcd_solver_stats *stats, void *stream);
 
+/* ----------------------------------------------------------------- server */
+
+/* A solve server: independent even-odd CG solves of different volumes and
+ * parameters, admitted as slots and device memory free up and run
+ * concurrently, one CUDA stream per slot.  The paper notes that
+ * finite-temperature studies are a naturally parallel set of independent
+ * simulations over couplings and volumes (Sec. 1), bounded by device memory
+ * (Sec. 2).  Gauge fields stay resident (registered once, shared read-only);
+ * each slot keeps per-volume solver contexts; a request is admitted in
+ * arrival order when a slot is free and its context fits memory_budget
+ * (idle contexts of that slot are released to make room).  A solve's result
+ * does not depend on what else runs (same kernels, launch shapes and
+ * fixed-order reductions).  All entry points are thread-safe. */
+typedef struct qcd_server qcd_server;
+typedef struct {
+    int slots;             /* concurrent solves (1..64) */
+    size_t memory_budget;  /* device bytes the solver contexts may use */
+} qcd_server_config;
+typedef struct {
+    int gauge_id;          /* from qcd_server_add_gauge */
+    double kappa, mu, tol;
+    int maxiter;
+    qcd_prec inner_prec;   /* as qcd_solver_params (even-odd solve of M x = b) */
+    qcd_recon inner_recon;
+    double reliable_delta;
+    const double *b_host;  /* full source, host layout; valid until the request completes */
+    double *x_host;        /* full solution, written before completion */
+} qcd_request;
+typedef struct {
+    long long id;
+    int status;            /* the solve's qcd_status */
+    int slot;
+    qcd_solver_stats stats;
+    double t_submit, t_start, t_end; /* seconds since qcd_server_create */
+} qcd_request_result;
+/* Errors: INVALID_ARG; CUDA (stream creation). */
+qcd_status qcd_server_create(const qcd_server_config *cfg, qcd_server **out);
+/* Register a resident F64 gauge field (the caller keeps it alive and
+ * unchanged while the server runs; prepare the inner precisions with
+ * qcd_gauge_prepare first). */
+qcd_status qcd_server_add_gauge(qcd_server *sv, const qcd_gauge *g, int *gauge_id);
+/* Queue a request; returns at once with its id.  OOM if the request alone
+ * needs more than the whole budget. */
+qcd_status qcd_server_submit(qcd_server *sv, const qcd_request *req, long long *request_id);
+/* Block until the request completes; fills `out` and forgets the request. */
+qcd_status qcd_server_wait(qcd_server *sv, long long request_id, qcd_request_result *out);
+/* Bytes reserved by solver contexts, queued and running request counts. */
+qcd_status qcd_server_info(qcd_server *sv, size_t *used_bytes, int *queued, int *running);
+/* Stop the workers (after their current request) and free the contexts;
+ * requests not yet waited for are dropped. */
+void qcd_server_destroy(qcd_server *sv);
+
 /* ------------------------------------------------------------ measurement */
 
 /* The paper's kernel classes carry the number of FLOPs each kernel performs

@@ -16,6 +16,12 @@ namespace qcd {
 static thread_local char g_err[512] = "";
 static std::atomic<unsigned long long> g_launches{0};
 
+std::shared_mutex &device_mutex()
+{
+    static std::shared_mutex m;
+    return m;
+}
+
 void note_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 
 // ---- hopping-kernel profiling (qcd_profile_begin / qcd_profile_end)
@@ -111,6 +117,7 @@ void *workspace(const qcd_lattice *lat, const std::string &name, size_t bytes)
 {
     auto it = lat->ws.find(name);
     if (it != lat->ws.end() && it->second.second >= bytes) return it->second.first;
+    DeviceLock dl(device_mutex());
     if (it != lat->ws.end()) {
         // cached CG graphs may hold this buffer's address: drop them all
         cudaDeviceSynchronize();
@@ -186,10 +193,13 @@ GaugeView gauge_view(const qcd_gauge *g, int prec, int recon, cudaStream_t s, qc
     if (prec == g->prec && recon == g->recon) return GaugeView{g->data, stride};
     const int key = prec * 100 + recon;
     auto *gm = const_cast<qcd_gauge *>(g);
+    static std::mutex derived_mu;  // concurrent solves may share one gauge field
+    std::lock_guard<std::mutex> lk(derived_mu);
     auto it = gm->derived.find(key);
     if (it != gm->derived.end()) return GaugeView{it->second.first, stride};
     const size_t bytes = gauge_bytes(prec, recon, stride);
     void *p = nullptr;
+    DeviceLock dl(device_mutex());
     if (cudaMalloc(&p, bytes) != cudaSuccess) {
         cudaGetLastError();
         *st = fail(QCD_ERR_OOM, "gauge copy: cudaMalloc(%zu) failed", bytes);
@@ -517,6 +527,7 @@ qcd_status qcd_lattice_create(const int dims[4], int t_bc, qcd_lattice **out)
         return fail(QCD_ERR_INVALID_ARG, "lattice_create: volume too large");
     qcd_lattice *lat = new (std::nothrow) qcd_lattice();
     if (!lat) return fail(QCD_ERR_OOM, "lattice_create: host allocation");
+    DeviceLock dl(device_mutex());
     memcpy(lat->dims, dims, sizeof(lat->dims));
     lat->t_bc = t_bc;
     cudaGetDevice(&lat->device);
@@ -543,9 +554,9 @@ qcd_status qcd_lattice_create(const int dims[4], int t_bc, qcd_lattice **out)
     if (e == cudaSuccess) e = cudaMallocHost(&lat->state_host, sizeof(CgState));
     if (e == cudaSuccess) e = cudaMemset(lat->red_counter, 0, 64);
     if (e == cudaSuccess) e = cudaMemset(lat->state, 0, sizeof(CgState));
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         qcd_status st = check_cuda(e, "lattice_create");
+        dl.unlock();
         qcd_lattice_destroy(lat);
         return st;
     }
@@ -556,6 +567,7 @@ qcd_status qcd_lattice_create(const int dims[4], int t_bc, qcd_lattice **out)
 void qcd_lattice_destroy(qcd_lattice *lat)
 {
     if (!lat) return;
+    DeviceLock dl(device_mutex());
     cudaDeviceSynchronize();
     cudaFree(lat->red_partials);
     cudaFree(lat->red_counter);
@@ -583,6 +595,7 @@ qcd_status qcd_gauge_create(const qcd_lattice *lat, qcd_prec prec, qcd_recon rec
     g->prec = prec;
     g->recon = recon;
     g->bytes = gauge_bytes(prec, recon, lat->stride);
+    DeviceLock dl(device_mutex());
     if (cudaMalloc(&g->data, g->bytes) != cudaSuccess) {
         cudaGetLastError();
         delete g;
@@ -606,6 +619,7 @@ qcd_status qcd_gauge_upload(qcd_gauge *g, const double *host, void *stream)
     const size_t bytes = (size_t)g->lat->h * 2 * 4 * 9 * 16;
     if (!g->derived.empty()) {
         cudaStreamSynchronize(s);
+        DeviceLock dl(device_mutex());
         drop_derived(g);
     }
     void *stage = nullptr;
@@ -632,6 +646,7 @@ qcd_status qcd_gauge_prepare(qcd_gauge *g, qcd_prec prec, qcd_recon recon, void 
 void qcd_gauge_destroy(qcd_gauge *g)
 {
     if (!g) return;
+    DeviceLock dl(device_mutex());
     cudaDeviceSynchronize();
     drop_derived(g);
     cudaFree(g->data);
@@ -669,6 +684,7 @@ qcd_status qcd_spinor_create(const qcd_lattice *lat, qcd_parity parity, qcd_prec
     qcd_spinor *s = new_spinor(lat, parity, prec);
     if (!s) return fail(QCD_ERR_OOM, "spinor_create: host allocation");
     const int nh = parity == QCD_PARITY_FULL ? 2 : 1;
+    DeviceLock dl(device_mutex());
     cudaError_t e = cudaMalloc(&s->data, nh * s->half_data_bytes);
     if (e == cudaSuccess && s->half_norm_bytes) e = cudaMalloc(reinterpret_cast<void **>(&s->norm), nh * s->half_norm_bytes);
     if (e == cudaSuccess) e = cudaMemset(s->data, 0, nh * s->half_data_bytes);
@@ -706,6 +722,7 @@ void qcd_spinor_destroy(qcd_spinor *s)
 {
     if (!s) return;
     if (s->owns) {
+        DeviceLock dl(device_mutex());
         cudaDeviceSynchronize();
         cudaFree(s->data);
         cudaFree(s->norm);

@@ -2,6 +2,8 @@
 #pragma once
 
 #include <map>
+#include <mutex>
+#include <shared_mutex>
 #include <string>
 
 #include "qcd_ops.h"
@@ -58,6 +60,15 @@ struct qcd_spinor {
 
 namespace qcd {
 
+// Graph capture vs device-wide operations.  A CUDA graph capture on one
+// thread is invalidated when another thread synchronises the whole device or
+// frees memory meanwhile.  Captures hold this lock shared (several may run
+// at once); every call that allocates, frees or synchronises the device
+// holds it exclusively.
+std::shared_mutex &device_mutex();
+using CaptureLock = std::shared_lock<std::shared_mutex>;
+using DeviceLock = std::unique_lock<std::shared_mutex>;
+
 // True inside a qcd_profile_begin/end window (per-launch events cannot be
 // captured into conditional graph bodies, so the solver runs eagerly then).
 bool profiling_active();
@@ -107,6 +118,11 @@ struct HopArgs {
     const Reduction *red;  // scratch of the fused reduction (nullptr: the lattice's)
 };
 cudaError_t hop(const qcd_lattice *lat, const GaugeView &U, int recon, const HopArgs &h, cudaStream_t s);
+
+// The CG solve behind qcd_solve_cg / qcd_solve_cg_multi, with an optional
+// context lattice (scratch, state, graphs) other than the gauge field's.
+qcd_status solve_impl(const qcd_gauge *g, qcd_spinor *const *x, const qcd_spinor *const *b, int nrhs,
+                      const qcd_solver_params *prm, qcd_solver_stats *stats, cudaStream_t s, const qcd_lattice *ctx);
 
 // Autotuned threads per block of the hopping kernel for this configuration
 // (times the candidates on first use outside stream capture).

@@ -1,0 +1,289 @@
+// Solve server: a request loop that admits CG solves as slots and device
+// memory free up and runs them concurrently on the GPU.
+//
+// The paper points out that finite-temperature studies form a naturally
+// parallel setup of many independent simulations over couplings and volumes
+// (Sec. 1), and that device memory bounds what can run (Sec. 2).  Here many
+// independent inversions of different volumes and hopping parameters share
+// one GPU:
+//   * gauge fields stay resident (registered once, shared read-only);
+//   * `slots` worker threads each own a CUDA stream and, per lattice volume,
+//     a solver context (lattice scratch, CG state, cached CG graph, device
+//     b and x);
+//   * requests queue in arrival order; the head request is admitted to a
+//     free slot as soon as the memory its context needs fits the budget
+//     (idle contexts of that slot are released to make room), so requests
+//     that arrive while others run start as soon as a slot and memory free
+//     up, and their kernels overlap with the running ones on the device;
+//   * each request records submit, start and end times for latency.
+// Results do not depend on what else runs: a solve's kernels, launch shapes
+// and fixed-order reductions are the same alone and in the mix.
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "qcd_handles.h"
+
+namespace {
+
+using clock_type = std::chrono::steady_clock;
+
+struct VolumeCtx {
+    qcd_lattice *lat = nullptr;
+    qcd_spinor *b = nullptr, *x = nullptr;
+    size_t reserved = 0;  // bytes counted against the budget
+};
+
+struct Job {
+    long long id;
+    qcd_request req;
+    double t_submit = 0, t_start = 0, t_end = 0;
+    int status = QCD_OK;
+    int slot = -1;
+    qcd_solver_stats stats{};
+    bool done = false;
+};
+
+std::string dims_key(const qcd_lattice *l)
+{
+    return std::to_string(l->dims[0]) + "x" + std::to_string(l->dims[1]) + "x" + std::to_string(l->dims[2]) + "x" +
+           std::to_string(l->dims[3]) + (l->t_bc < 0 ? "a" : "p");
+}
+
+// Device bytes of one solver context: b, x (FULL FP64) and the solver's
+// workspace (FP64 and inner fields, operator temporaries, residual fields,
+// staging), bounded by 24 FP64 full fields.
+size_t context_bytes(const qcd_lattice *l) { return (size_t)24 * 2 * l->h * 192; }
+
+}  // namespace
+
+struct qcd_server {
+    int device = 0;
+    size_t budget = 0, used = 0;
+    int nslots = 0;
+    clock_type::time_point t0;
+    std::vector<const qcd_gauge *> gauges;
+    std::deque<Job *> queue;
+    std::map<long long, Job *> jobs;
+    long long next_id = 1;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    bool stop = false;
+    std::vector<std::thread> workers;
+    std::vector<std::map<std::string, VolumeCtx>> slot_ctx;
+    std::vector<cudaStream_t> streams;
+    std::vector<int> busy;
+
+    double now() const { return std::chrono::duration<double>(clock_type::now() - t0).count(); }
+};
+
+namespace {
+
+void release(qcd_server *sv, VolumeCtx &c)
+{
+    qcd_spinor_destroy(c.b);
+    qcd_spinor_destroy(c.x);
+    qcd_lattice_destroy(c.lat);
+    sv->used -= c.reserved;
+    c = VolumeCtx{};
+}
+
+// Under sv->mu: can slot `s` take job `j` now?  Reserves memory if so.
+bool admit(qcd_server *sv, int s, Job *j)
+{
+    const qcd_lattice *gl = sv->gauges[j->req.gauge_id]->lat;
+    const std::string key = dims_key(gl);
+    auto &ctxs = sv->slot_ctx[s];
+    if (ctxs.count(key)) return true;
+    const size_t need = context_bytes(gl);
+    // release this slot's idle contexts of other volumes until it fits
+    for (auto it = ctxs.begin(); sv->used + need > sv->budget && it != ctxs.end();) {
+        release(sv, it->second);
+        it = ctxs.erase(it);
+    }
+    if (sv->used + need > sv->budget) return false;
+    sv->used += need;
+    ctxs[key].reserved = need;
+    return true;
+}
+
+void run_job(qcd_server *sv, int s, Job *j)
+{
+    cudaSetDevice(sv->device);
+    const qcd_gauge *g = sv->gauges[j->req.gauge_id];
+    VolumeCtx *c;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        c = &sv->slot_ctx[s][dims_key(g->lat)];
+    }
+    qcd_status st = QCD_OK;
+    if (!c->lat) {
+        st = qcd_lattice_create(g->lat->dims, g->lat->t_bc, &c->lat);
+        if (st == QCD_OK) st = qcd_spinor_create(c->lat, QCD_PARITY_FULL, QCD_PREC_F64, &c->b);
+        if (st == QCD_OK) st = qcd_spinor_create(c->lat, QCD_PARITY_FULL, QCD_PREC_F64, &c->x);
+    }
+    cudaStream_t stream = sv->streams[s];
+    if (st == QCD_OK) st = qcd_spinor_upload(c->b, j->req.b_host, stream);
+    if (st == QCD_OK) {
+        const qcd_request &r = j->req;
+        qcd_solver_params prm{r.kappa, r.mu, r.tol, r.maxiter, 1, 0, r.inner_prec, r.inner_recon, r.reliable_delta};
+        qcd_spinor *xs[1] = {c->x};
+        const qcd_spinor *bs[1] = {c->b};
+        st = qcd::solve_impl(g, xs, bs, 1, &prm, &j->stats, stream, c->lat);
+        // NOT_CONVERGED still returns x
+        if (st == QCD_OK || st == QCD_ERR_NOT_CONVERGED) {
+            qcd_status st2 = qcd_spinor_download(c->x, j->req.x_host, stream);
+            if (st2 == QCD_OK) st2 = qcd_stream_sync(stream);
+            if (st2 != QCD_OK) st = st2;
+        }
+    }
+    j->status = st;
+}
+
+void worker(qcd_server *sv, int s)
+{
+    cudaSetDevice(sv->device);
+    std::unique_lock<std::mutex> lk(sv->mu);
+    for (;;) {
+        sv->cv_work.wait(lk, [&] { return sv->stop || !sv->queue.empty(); });
+        if (sv->stop) return;
+        Job *j = sv->queue.front();
+        if (!admit(sv, s, j)) {  // wait for memory to free up, then retry
+            sv->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+            continue;
+        }
+        sv->queue.pop_front();
+        sv->busy[s] = 1;
+        j->slot = s;
+        j->t_start = sv->now();
+        lk.unlock();
+        run_job(sv, s, j);
+        lk.lock();
+        j->t_end = sv->now();
+        j->done = true;
+        sv->busy[s] = 0;
+        sv->cv_done.notify_all();
+        sv->cv_work.notify_all();
+    }
+}
+
+}  // namespace
+
+using qcd::fail;
+
+extern "C" {
+
+qcd_status qcd_server_create(const qcd_server_config *cfg, qcd_server **out)
+{
+    if (!cfg || !out) return fail(QCD_ERR_INVALID_ARG, "server_create: NULL argument");
+    *out = nullptr;
+    if (cfg->slots < 1 || cfg->slots > 64 || cfg->memory_budget == 0)
+        return fail(QCD_ERR_INVALID_ARG, "server_create: slots must be 1..64 and the budget positive");
+    auto *sv = new (std::nothrow) qcd_server();
+    if (!sv) return fail(QCD_ERR_OOM, "server_create: host allocation");
+    cudaGetDevice(&sv->device);
+    sv->budget = cfg->memory_budget;
+    sv->nslots = cfg->slots;
+    sv->t0 = clock_type::now();
+    sv->slot_ctx.resize(cfg->slots);
+    sv->busy.assign(cfg->slots, 0);
+    for (int s = 0; s < cfg->slots; ++s) {
+        cudaStream_t st;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            for (cudaStream_t x : sv->streams) cudaStreamDestroy(x);
+            delete sv;
+            return fail(QCD_ERR_CUDA, "server_create: cudaStreamCreate failed");
+        }
+        sv->streams.push_back(st);
+    }
+    for (int s = 0; s < cfg->slots; ++s) sv->workers.emplace_back(worker, sv, s);
+    *out = sv;
+    return QCD_OK;
+}
+
+qcd_status qcd_server_add_gauge(qcd_server *sv, const qcd_gauge *g, int *gauge_id)
+{
+    if (!sv || !g || !gauge_id) return fail(QCD_ERR_INVALID_ARG, "server_add_gauge: NULL argument");
+    if (g->prec != QCD_PREC_F64) return fail(QCD_ERR_INVALID_ARG, "server_add_gauge: the gauge field must be F64");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->gauges.push_back(g);
+    *gauge_id = (int)sv->gauges.size() - 1;
+    return QCD_OK;
+}
+
+qcd_status qcd_server_submit(qcd_server *sv, const qcd_request *req, long long *request_id)
+{
+    if (!sv || !req || !request_id) return fail(QCD_ERR_INVALID_ARG, "server_submit: NULL argument");
+    if (!req->b_host || !req->x_host) return fail(QCD_ERR_INVALID_ARG, "server_submit: NULL host buffer");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (req->gauge_id < 0 || req->gauge_id >= (int)sv->gauges.size())
+        return fail(QCD_ERR_INVALID_ARG, "server_submit: unknown gauge id %d", req->gauge_id);
+    if (context_bytes(sv->gauges[req->gauge_id]->lat) > sv->budget)
+        return fail(QCD_ERR_OOM, "server_submit: the request needs more device memory than the whole budget");
+    Job *j = new Job();
+    j->id = sv->next_id++;
+    j->req = *req;
+    j->t_submit = sv->now();
+    sv->jobs[j->id] = j;
+    sv->queue.push_back(j);
+    *request_id = j->id;
+    sv->cv_work.notify_all();
+    return QCD_OK;
+}
+
+qcd_status qcd_server_wait(qcd_server *sv, long long request_id, qcd_request_result *out)
+{
+    if (!sv || !out) return fail(QCD_ERR_INVALID_ARG, "server_wait: NULL argument");
+    std::unique_lock<std::mutex> lk(sv->mu);
+    auto it = sv->jobs.find(request_id);
+    if (it == sv->jobs.end()) return fail(QCD_ERR_INVALID_ARG, "server_wait: unknown request %lld", request_id);
+    Job *j = it->second;
+    sv->cv_done.wait(lk, [&] { return j->done; });
+    out->id = j->id;
+    out->status = j->status;
+    out->stats = j->stats;
+    out->t_submit = j->t_submit;
+    out->t_start = j->t_start;
+    out->t_end = j->t_end;
+    out->slot = j->slot;
+    sv->jobs.erase(it);
+    delete j;
+    return QCD_OK;
+}
+
+qcd_status qcd_server_info(qcd_server *sv, size_t *used_bytes, int *queued, int *running)
+{
+    if (!sv) return fail(QCD_ERR_INVALID_ARG, "server_info: NULL argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (used_bytes) *used_bytes = sv->used;
+    if (queued) *queued = (int)sv->queue.size();
+    if (running) {
+        int r = 0;
+        for (int b : sv->busy) r += b;
+        *running = r;
+    }
+    return QCD_OK;
+}
+
+void qcd_server_destroy(qcd_server *sv)
+{
+    if (!sv) return;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+        sv->cv_work.notify_all();
+    }
+    for (auto &t : sv->workers) t.join();
+    cudaSetDevice(sv->device);
+    for (auto &m : sv->slot_ctx)
+        for (auto &kv : m) release(sv, kv.second);
+    for (cudaStream_t s : sv->streams) cudaStreamDestroy(s);
+    for (auto &kv : sv->jobs) delete kv.second;
+    delete sv;
+}
+
+}  // extern "C"

@@ -246,6 +246,7 @@ qcd_status cg_graph(const qcd_lattice *lat, const CgFields &f, cudaGraphExec_t *
         if (e != cudaSuccess) return check_cuda(e, "solve_cg: capture stream");
     }
     cudaStream_t cs = lat->capture_stream;
+    CaptureLock cl(device_mutex());  // no device-wide call may run during the capture
     cudaGraph_t g = nullptr, tmp = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaGraphConditionalHandle hloop, hrel;
@@ -272,6 +273,8 @@ qcd_status cg_graph(const qcd_lattice *lat, const CgFields &f, cudaGraphExec_t *
         cudaError_t ec = enqueue_iteration(f, cs);
         if (ec == cudaSuccess) ec = launch_cg_ctrl_reliable(f.state, hrel, cs);
         if (ec == cudaSuccess) ec = cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &ndeps);
+        if (ec == cudaSuccess && cst != cudaStreamCaptureStatusActive) ec = cudaErrorStreamCaptureInvalidated;
+        if (ec == cudaSuccess && ndeps > 0 && !deps) ec = cudaErrorStreamCaptureInvalidated;
         if (ec == cudaSuccess) tail.assign(deps, deps + ndeps);
         cudaError_t ee = cudaStreamEndCapture(cs, &tmp);
         e = ec != cudaSuccess ? ec : ee;
@@ -342,13 +345,23 @@ FieldView half_of(const FieldView &f, int k)
 
 // The solve for nrhs right-hand sides in one batched CG (nrhs = 1: the
 // caller's fields are used in place).
-qcd_status solve_impl(const qcd_gauge *g, qcd_spinor *const *x, const qcd_spinor *const *b, int nrhs,
-                      const qcd_solver_params *prm, qcd_solver_stats *stats, cudaStream_t s)
+}  // namespace
+
+// The solve for nrhs right-hand sides in one batched CG (nrhs = 1: the
+// caller's fields are used in place).  `ctx` is the lattice handle whose
+// scratch, CG state and graph cache the solve uses (nullptr: the gauge
+// field's own); it must have the gauge field's extents, and x, b must live
+// on it.  Separate contexts let solves that share one resident gauge field
+// run concurrently on different streams.
+qcd_status qcd::solve_impl(const qcd_gauge *g, qcd_spinor *const *x, const qcd_spinor *const *b, int nrhs,
+                      const qcd_solver_params *prm, qcd_solver_stats *stats, cudaStream_t s, const qcd_lattice *ctx)
 {
     const auto t0 = std::chrono::steady_clock::now();
     if (!g || !x || !b || !prm) return fail(QCD_ERR_INVALID_ARG, "solve_cg: NULL argument");
     if (nrhs < 1 || nrhs > kMaxRhs) return fail(QCD_ERR_INVALID_ARG, "solve_cg: nrhs = %d not in 1..%d", nrhs, kMaxRhs);
-    const qcd_lattice *lat = g->lat;
+    const qcd_lattice *lat = ctx ? ctx : g->lat;
+    if (memcmp(lat->dims, g->lat->dims, sizeof(lat->dims)) != 0 || lat->t_bc != g->lat->t_bc)
+        return fail(QCD_ERR_INVALID_ARG, "solve_cg: the context lattice differs from the gauge field's");
     for (int k = 0; k < nrhs; ++k) {
         if (!x[k] || !b[k]) return fail(QCD_ERR_INVALID_ARG, "solve_cg: NULL field");
         if (x[k]->lat != lat || b[k]->lat != lat) return fail(QCD_ERR_INVALID_ARG, "solve_cg: lattices differ");
@@ -490,8 +503,12 @@ qcd_status solve_impl(const qcd_gauge *g, qcd_spinor *const *x, const qcd_spinor
         // choose the inner kernels' launch shape before it is frozen in the graph
         tuned_tpb(lat, Us, sp, srecon, L, !c.eo, s);
         cudaGraphExec_t exec = nullptr;
-        qcd_status gst = cg_graph(lat, F, &exec);
-        if (gst != QCD_OK) return gst;
+        if (cg_graph(lat, F, &exec) != QCD_OK) {
+            // the capture failed (e.g. invalidated by another thread): run
+            // the same kernels eagerly instead
+            QCD_TRY(cg_eager(lat, F, s), "solve_cg: iterations");
+            goto after_loop;
+        }
         QCD_TRY(cudaGraphLaunch(exec, s), "solve_cg: graph launch");
         QCD_TRY(read_state(lat, s), "solve_cg: state");
         // kernels the graph ran: per trip the iteration and two control
@@ -501,6 +518,7 @@ qcd_status solve_impl(const qcd_gauge *g, qcd_spinor *const *x, const qcd_spinor
     } else {
         QCD_TRY(cg_eager(lat, F, s), "solve_cg: iterations");
     }
+after_loop:
     const CgState hs = *lat->state_host;
     if (hs.status == CG_BREAKDOWN)
         result = fail(QCD_ERR_BREAKDOWN, "solve_cg: breakdown (non-positive <p,Ap> or non-finite values)");
@@ -566,19 +584,17 @@ qcd_status solve_impl(const qcd_gauge *g, qcd_spinor *const *x, const qcd_spinor
     return result;
 }
 
-}  // namespace
-
 extern "C" qcd_status qcd_solve_cg(const qcd_gauge *g, qcd_spinor *x, const qcd_spinor *b,
                                    const qcd_solver_params *prm, qcd_solver_stats *stats, void *stream)
 {
     qcd_spinor *xs[1] = {x};
     const qcd_spinor *bs[1] = {b};
-    return solve_impl(g, xs, bs, 1, prm, stats, static_cast<cudaStream_t>(stream));
+    return solve_impl(g, xs, bs, 1, prm, stats, static_cast<cudaStream_t>(stream), nullptr);
 }
 
 extern "C" qcd_status qcd_solve_cg_multi(const qcd_gauge *g, qcd_spinor *const *x, const qcd_spinor *const *b,
                                          int nrhs, const qcd_solver_params *prm, qcd_solver_stats *stats,
                                          void *stream)
 {
-    return solve_impl(g, x, b, nrhs, prm, stats, static_cast<cudaStream_t>(stream));
+    return solve_impl(g, x, b, nrhs, prm, stats, static_cast<cudaStream_t>(stream), nullptr);
 }

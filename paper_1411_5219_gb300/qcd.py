@@ -46,6 +46,20 @@ class Profile(ctypes.Structure):
     _fields_ = [("prec", ProfileEntry * 5)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("slots", _i), ("memory_budget", ctypes.c_size_t)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("gauge_id", _i), ("kappa", _d), ("mu", _d), ("tol", _d), ("maxiter", _i), ("inner_prec", _i),
+                ("inner_recon", _i), ("reliable_delta", _d), ("b_host", _p), ("x_host", _p)]
+
+
+class RequestResult(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_longlong), ("status", _i), ("slot", _i), ("stats", SolverStats),
+                ("t_submit", _d), ("t_start", _d), ("t_end", _d)]
+
+
 # name -> (restype, argtypes); mirrors include/qcd.h
 _SIGS = {
     "qcd_status_string": (ctypes.c_char_p, [_i]),
@@ -74,6 +88,12 @@ _SIGS = {
     "qcd_profile_end": (_i, [ctypes.POINTER(Profile)]),
     "qcd_kernel_launches": (ctypes.c_ulonglong, []),
     "qcd_norm2_noalloc": (_i, [_p, ctypes.c_size_t, _p, _p]),
+    "qcd_server_create": (_i, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_p)]),
+    "qcd_server_add_gauge": (_i, [_p, _p, ctypes.POINTER(_i)]),
+    "qcd_server_submit": (_i, [_p, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_longlong)]),
+    "qcd_server_wait": (_i, [_p, ctypes.c_longlong, ctypes.POINTER(RequestResult)]),
+    "qcd_server_info": (_i, [_p, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "qcd_server_destroy": (None, [_p]),
     "qcd_apply_dslash_multi": (_i, [_p, ctypes.POINTER(_p), ctypes.POINTER(_p), _i, _i, _p]),
     "qcd_solve_cg_multi": (_i, [_p, ctypes.POINTER(_p), ctypes.POINTER(_p), _i, ctypes.POINTER(SolverParams),
                                 ctypes.POINTER(SolverStats), _p]),
@@ -349,3 +369,51 @@ def norm2_noalloc(x_ptr: int, n: int, result_ptr: int, stream=None):
     """qcd_norm2_noalloc on raw device pointers (no allocation in the library)."""
     _check(lib().qcd_norm2_noalloc(_p(x_ptr), ctypes.c_size_t(n), _p(result_ptr), _stream(stream)),
            "qcd_norm2_noalloc")
+
+
+class Server:
+    """qcd_server: concurrent even-odd solves admitted by slot and memory budget."""
+
+    def __init__(self, slots: int = 4, memory_budget: int = 32 << 30):
+        h = _p()
+        _check(lib().qcd_server_create(ctypes.byref(ServerConfig(int(slots), int(memory_budget))), ctypes.byref(h)),
+               "qcd_server_create")
+        self._h = h
+        self._keep = {}
+
+    def add_gauge(self, gauge: Gauge) -> int:
+        gid = _i()
+        _check(lib().qcd_server_add_gauge(self._h, gauge.handle, ctypes.byref(gid)), "qcd_server_add_gauge")
+        self._keep[("g", gid.value)] = gauge
+        return gid.value
+
+    def submit(self, gauge_id: int, b_host, x_host, kappa: float, mu: float = 0.0, tol: float = 1e-10,
+               maxiter: int = 20000, inner_prec: str = "f16", inner_recon: int = 12,
+               reliable_delta: float = 0.1) -> int:
+        req = Request(int(gauge_id), float(kappa), float(mu), float(tol), int(maxiter), PREC[inner_prec],
+                      int(inner_recon), float(reliable_delta), _host_ptr(b_host), _host_ptr(x_host))
+        rid = ctypes.c_longlong()
+        _check(lib().qcd_server_submit(self._h, ctypes.byref(req), ctypes.byref(rid)), "qcd_server_submit")
+        self._keep[rid.value] = (b_host, x_host)
+        return rid.value
+
+    def wait(self, request_id: int) -> dict:
+        res = RequestResult()
+        _check(lib().qcd_server_wait(self._h, int(request_id), ctypes.byref(res)), "qcd_server_wait")
+        self._keep.pop(request_id, None)
+        out = {k: getattr(res, k) for k, _ in RequestResult._fields_ if k != "stats"}
+        out["stats"] = {k: getattr(res.stats, k) for k, _ in SolverStats._fields_}
+        return out
+
+    def info(self):
+        used, q, r = ctypes.c_size_t(), _i(), _i()
+        _check(lib().qcd_server_info(self._h, ctypes.byref(used), ctypes.byref(q), ctypes.byref(r)), "qcd_server_info")
+        return {"used_bytes": used.value, "queued": q.value, "running": r.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().qcd_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()

@@ -89,7 +89,7 @@ def gaussian_complex(seed: int, stream: int, shape, start: int = 0) -> np.ndarra
     return (g[0::2] + 1j * g[1::2]).reshape(shape)
 
 
-def su3_near_unit(seed: int, stream: int, n: int, eps: float, chunk: int = 1 << 18) -> np.ndarray:
+def su3_near_unit(seed: int, stream: int, n: int, eps: float, chunk: int = 1 << 18, device=None) -> np.ndarray:
     """n SU(3) matrices U = exp(i*eps*H), H Hermitian traceless, Gaussian.
 
     For matrix j, a 3x3 complex Gaussian A (counters 9j .. 9j+8 of the
@@ -105,17 +105,26 @@ def su3_near_unit(seed: int, stream: int, n: int, eps: float, chunk: int = 1 << 
         h = 0.5 * (a + np.conj(np.swapaxes(a, 1, 2)))
         tr = np.trace(h, axis1=1, axis2=2).real / 3.0
         h = h - tr[:, None, None] * np.eye(3)
-        lam, v = np.linalg.eigh(h)
-        ph = np.exp(1j * eps * lam)
-        out[s:s + m] = np.einsum("nab,nb,ncb->nac", v, ph, np.conj(v))
+        if device is None:
+            lam, v = np.linalg.eigh(h)
+            ph = np.exp(1j * eps * lam)
+            out[s:s + m] = np.einsum("nab,nb,ncb->nac", v, ph, np.conj(v))
+        else:  # the same Gaussian draws, exp(i eps H) by torch's matrix exponential on a device
+            import torch
+            ht = torch.from_numpy(h).to(device)
+            out[s:s + m] = torch.linalg.matrix_exp(1j * eps * ht).cpu().numpy()
     return out
 
 
-def gauge_field(dims, eps: float, seed: int) -> np.ndarray:
-    """Near-unit random gauge field U[t,z,y,x,mu,3,3], one draw per (site, mu)."""
+def gauge_field(dims, eps: float, seed: int, device=None) -> np.ndarray:
+    """Near-unit random gauge field U[t,z,y,x,mu,3,3], one draw per (site, mu).
+
+    device: None for numpy, or a torch device on which exp(i eps H) of the
+    same draws is taken by matrix exponential (faster for large lattices; the
+    links agree with the numpy ones to rounding)."""
     lx, ly, lz, lt = check_dims(dims)
     v = volume(dims)
-    u = su3_near_unit(seed, STREAM_GAUGE, 4 * v, eps)
+    u = su3_near_unit(seed, STREAM_GAUGE, 4 * v, eps, device=device)
     return u.reshape(lt, lz, ly, lx, 4, 3, 3)
 
 

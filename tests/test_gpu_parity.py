@@ -556,3 +556,73 @@ def test_autotuner_file_cache(tmp_path):
     assert len(lines) == 2 and lines[0].startswith("dslash:p1:r12:n0:b0:8x8x8x4") and lines[1] in ("64", "128", "256")
     subprocess.run([sys.executable, "-c", code], check=True, env=env)
     assert cache.read_text().split() == lines
+
+
+# ----------------------------------------------------------------- server
+
+def _server_problem(q, dims, seed):
+    lat = q.Lattice(dims, -1)
+    U = syn.gauge_field(dims, 0.2, seed)
+    g = q.Gauge(lat, "f64", 18)
+    g.upload(U)
+    g.prepare("f16", 12)
+    return lat, U, g
+
+
+def test_server_same_alone_and_in_mix(q):
+    """Each request's solution is bit for bit the same when it runs alone and
+    when it runs concurrently with other requests of other volumes."""
+    probs = [_server_problem(q, d, 300 + k) for k, d in enumerate([(8, 8, 8, 4), (12, 12, 12, 4), (16, 16, 16, 8)])]
+    sv = q.Server(slots=4, memory_budget=8 << 30)
+    gids = [sv.add_gauge(p[2]) for p in probs]
+    reqs = []
+    for k in range(9):
+        pi = k % 3
+        dims = probs[pi][0].dims
+        b = syn.gaussian_spinor(dims, 400 + k)
+        reqs.append((pi, b, 0.12 + 0.005 * k))
+    alone = []
+    for pi, b, kappa in reqs:
+        x = np.empty_like(b)
+        r = sv.wait(sv.submit(gids[pi], b, x, kappa, inner_prec="f16"))
+        assert r["status"] == 0 and r["stats"]["true_rel_residual"] <= 1e-10
+        alone.append(x)
+    xs = [np.empty_like(b) for _, b, _ in reqs]
+    ids = [sv.submit(gids[pi], b, xs[k], kappa, inner_prec="f16") for k, (pi, b, kappa) in enumerate(reqs)]
+    res = [sv.wait(i) for i in ids]
+    for k in range(len(reqs)):
+        assert res[k]["status"] == 0
+        assert np.array_equal(xs[k], alone[k]), k
+    pi, b, kappa = reqs[4]
+    assert schur_residual_oracle(probs[pi][1], b, xs[4], kappa, 0.0) <= 1.5e-10
+    sv.close()
+
+
+def test_server_overlap_and_memory_budget(q):
+    lat, U, g = _server_problem(q, (8, 8, 8, 4), 310)
+    lat2, U2, g2 = _server_problem(q, (16, 16, 16, 8), 311)
+    # a budget that holds one 16^3x8 context at a time: requests still finish
+    one_ctx = 24 * 2 * (16 ** 3 * 8 // 2) * 192
+    sv = q.Server(slots=4, memory_budget=one_ctx + 24 * 2 * (8 ** 3 * 4 // 2) * 192)
+    gid, gid2 = sv.add_gauge(g), sv.add_gauge(g2)
+    jobs = []
+    for k in range(12):
+        gg, d = (gid, (8, 8, 8, 4)) if k % 2 == 0 else (gid2, (16, 16, 16, 8))
+        b = syn.gaussian_spinor(d, 500 + k)
+        x = np.empty_like(b)
+        jobs.append((sv.submit(gg, b, x, 0.13, inner_prec="f16"), x))
+    res = [sv.wait(i) for i, _ in jobs]
+    assert all(r["status"] == 0 for r in res)
+    assert sv.info()["used_bytes"] <= one_ctx + 24 * 2 * (8 ** 3 * 4 // 2) * 192
+    # concurrency: some requests ran at the same time on different slots
+    iv = sorted((r["t_start"], r["t_end"], r["slot"]) for r in res)
+    overlaps = sum(1 for a, b_ in zip(iv, iv[1:]) if b_[0] < a[1] and b_[2] != a[2])
+    assert overlaps >= 1
+    big = q.Server(slots=1, memory_budget=1 << 20)
+    gbig = big.add_gauge(g2)
+    b = syn.gaussian_spinor((16, 16, 16, 8), 1)
+    with pytest.raises(q.QcdError) as e:
+        big.submit(gbig, b, np.empty_like(b), 0.13)
+    assert e.value.status == 2
+    sv.close()
+    big.close()
