@@ -281,7 +281,7 @@ def batched_block(qcd, torch, flush, hbm, reps):
     return res
 
 
-def serving_block(qcd, torch, n_requests=2000, rate=60.0, slots=8, seed=1006):
+def serving_block(qcd, torch, n_requests=2000, rate=30.0, slots=8, seed=1006):
     """configs[4]: a Poisson stream of even-odd solves of five volumes, kappa
     uniform in [0.12, 0.16], 3 resident gauge fields per volume, FP16-mixed
     CG to 1e-10, admitted by slot and device-memory budget."""

@@ -401,6 +401,7 @@ cudaError_t hop(const qcd_lattice *lat, const GaugeView &U, int recon, const Hop
     }
     memcpy(a.cy, h.cy.c, sizeof(a.cy));
     memcpy(a.cd, h.cd.c, sizeof(a.cd));
+    a.coef = h.coef;
     if (h.plain)
         a.epi = EPI_PLAIN;
     else if (!h.y)

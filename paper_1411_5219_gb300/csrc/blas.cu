@@ -140,6 +140,12 @@ __global__ void cg_state_init_kernel(CgState *s, int nrhs, double tol2, double d
     s->trip_limit = maxiter + 64;
 }
 
+__global__ void set_table_kernel(double *dst, const CoefTable t)
+{
+    const int k = threadIdx.x;
+    if (k < t.n) dst[k] = t.v[k];
+}
+
 // Graph control: run the reliable-update body when the iteration asked for it.
 __global__ void cg_ctrl_reliable_kernel(const CgState *st, cudaGraphConditionalHandle h)
 {
@@ -368,6 +374,13 @@ cudaError_t launch_diff_norm2(const FieldView &a, const FieldView &b, const Redu
 cudaError_t launch_cg_state_init(CgState *stt, int nrhs, double tol2, double delta2, int maxiter, cudaStream_t s)
 {
     cg_state_init_kernel<<<1, 1, 0, s>>>(stt, nrhs, tol2, delta2, maxiter);
+    note_launches();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_table(double *dst, const CoefTable &t, cudaStream_t s)
+{
+    set_table_kernel<<<1, 64, 0, s>>>(dst, t);
     note_launches();
     return cudaGetLastError();
 }

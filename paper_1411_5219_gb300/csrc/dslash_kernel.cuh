@@ -246,19 +246,28 @@ __global__ void __launch_bounds__(TPB, TPB == 64 ? dslash_min_blocks<SF>() : 1) 
         QCD_HOP(6, 3, SF_, false, false)
         QCD_HOP(7, 3, SB_, true, false)
 #undef QCD_HOP
+        // epilogue coefficients: kernel parameters, or a device table shared
+        // by every launch of a captured CG graph (so one graph serves all
+        // kappa and mu)
+        double cyv[2][2], cdv[2][2];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            cyv[k >> 1][k & 1] = a.coef ? __ldg(a.coef + k) : a.cy[k >> 1][k & 1];
+            cdv[k >> 1][k & 1] = a.coef ? __ldg(a.coef + 4 + k) : a.cd[k >> 1][k & 1];
+        }
         // epilogue
         Spinor<R> out;
         if (kEpi == EPI_PLAIN) {
             out = acc;
         } else if (kEpi == EPI_REAL_D) {
-            const R d = (R)a.cd[0][0];
+            const R d = (R)cdv[0][0];
 #pragma unroll
             for (int s = 0; s < 4; ++s)
 #pragma unroll
                 for (int cc = 0; cc < 3; ++cc) out.c[s][cc] = d * acc.c[s][cc];
         } else if (kEpi == EPI_REAL_YD) {
             const Spinor<R> y = SF::load(a.y[p], e);
-            const R cy = (R)a.cy[0][0], d = (R)a.cd[0][0];
+            const R cy = (R)cyv[0][0], d = (R)cdv[0][0];
 #pragma unroll
             for (int s = 0; s < 4; ++s)
 #pragma unroll
@@ -267,7 +276,7 @@ __global__ void __launch_bounds__(TPB, TPB == 64 ? dslash_min_blocks<SF>() : 1) 
                     out.c[s][cc].im = fma(d, acc.c[s][cc].im, cy * y.c[s][cc].im);
                 }
         } else {
-            const cx<R> d[2] = {mk((R)a.cd[0][0], (R)a.cd[0][1]), mk((R)a.cd[1][0], (R)a.cd[1][1])};
+            const cx<R> d[2] = {mk((R)cdv[0][0], (R)cdv[0][1]), mk((R)cdv[1][0], (R)cdv[1][1])};
             if (kEpi == EPI_CPLX_D) {
 #pragma unroll
                 for (int s = 0; s < 4; ++s)
@@ -275,7 +284,7 @@ __global__ void __launch_bounds__(TPB, TPB == 64 ? dslash_min_blocks<SF>() : 1) 
                     for (int cc = 0; cc < 3; ++cc) out.c[s][cc] = cmul(d[s >> 1], acc.c[s][cc]);
             } else {
                 const Spinor<R> y = SF::load(a.y[p], e);
-                const cx<R> cy[2] = {mk((R)a.cy[0][0], (R)a.cy[0][1]), mk((R)a.cy[1][0], (R)a.cy[1][1])};
+                const cx<R> cy[2] = {mk((R)cyv[0][0], (R)cyv[0][1]), mk((R)cyv[1][0], (R)cyv[1][1])};
 #pragma unroll
                 for (int s = 0; s < 4; ++s)
 #pragma unroll

@@ -116,6 +116,7 @@ struct HopArgs {
     FinalizeKind fin;
     bool check_status;
     const Reduction *red;  // scratch of the fused reduction (nullptr: the lattice's)
+    const double *coef;    // device table of cy, cd (8 doubles) read at run time, or nullptr
 };
 cudaError_t hop(const qcd_lattice *lat, const GaugeView &U, int recon, const HopArgs &h, cudaStream_t s);
 

@@ -948,6 +948,7 @@ struct DslashLaunch {
     GaugeView U;
     SpinorView in[2], out[2], y[2];
     double cy[2][2], cd[2][2];  // [chirality][re, im]
+    const double *coef;         // if set: cy, cd read from this device table (8 doubles) instead
     EpiMode epi;
     // optional fused |out|^2 reduction
     bool reduce;

@@ -48,6 +48,13 @@ cudaError_t launch_cg_accum_x(const FieldView &xhi, const FieldView &xs, cudaStr
 cudaError_t launch_cg_true_residual(const FieldView &rhs, const FieldView &q, const FieldView &rhi,
                                    const FieldView *rs, const Reduction &red, CgState *st, cudaStream_t s);
 
+// Small table of doubles written on the stream (kernel parameters -> device).
+struct CoefTable {
+    double v[64];
+    int n;
+};
+cudaError_t launch_set_table(double *dst, const CoefTable &t, cudaStream_t s);
+
 // Graph control kernels (cudaGraphSetConditional on the loop / reliable-update handles).
 cudaError_t launch_cg_ctrl_reliable(const CgState *st, cudaGraphConditionalHandle h, cudaStream_t s);
 cudaError_t launch_cg_ctrl_loop(CgState *st, cudaGraphConditionalHandle h, cudaStream_t s);

@@ -59,6 +59,9 @@ std::string dims_key(const qcd_lattice *l)
 // staging), bounded by 24 FP64 full fields.
 size_t context_bytes(const qcd_lattice *l) { return (size_t)24 * 2 * l->h * 192; }
 
+// Volumes up to 24^3 x 8 sites count as small (high-priority stream).
+constexpr size_t kSmallVolume = 24 * 24 * 24 * 8;
+
 }  // namespace
 
 struct qcd_server {
@@ -75,7 +78,8 @@ struct qcd_server {
     bool stop = false;
     std::vector<std::thread> workers;
     std::vector<std::map<std::string, VolumeCtx>> slot_ctx;
-    std::vector<cudaStream_t> streams;
+    std::vector<cudaStream_t> streams;     // per slot, high priority (small volumes)
+    std::vector<cudaStream_t> streams_lo;  // per slot, low priority (large volumes)
     std::vector<int> busy;
 
     double now() const { return std::chrono::duration<double>(clock_type::now() - t0).count(); }
@@ -126,7 +130,9 @@ void run_job(qcd_server *sv, int s, Job *j)
         if (st == QCD_OK) st = qcd_spinor_create(c->lat, QCD_PARITY_FULL, QCD_PREC_F64, &c->b);
         if (st == QCD_OK) st = qcd_spinor_create(c->lat, QCD_PARITY_FULL, QCD_PREC_F64, &c->x);
     }
-    cudaStream_t stream = sv->streams[s];
+    // Small volumes run on the slot's high-priority stream, so their few
+    // short kernels are not queued behind the long ones of large volumes.
+    cudaStream_t stream = (size_t)g->lat->h * 2 <= kSmallVolume ? sv->streams[s] : sv->streams_lo[s];
     if (st == QCD_OK) st = qcd_spinor_upload(c->b, j->req.b_host, stream);
     if (st == QCD_OK) {
         const qcd_request &r = j->req;
@@ -191,14 +197,20 @@ qcd_status qcd_server_create(const qcd_server_config *cfg, qcd_server **out)
     sv->t0 = clock_type::now();
     sv->slot_ctx.resize(cfg->slots);
     sv->busy.assign(cfg->slots, 0);
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
     for (int s = 0; s < cfg->slots; ++s) {
-        cudaStream_t st;
-        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStream_t hi = nullptr, lo = nullptr;
+        if (cudaStreamCreateWithPriority(&hi, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&lo, cudaStreamNonBlocking, prio_lo) != cudaSuccess) {
+            if (hi) cudaStreamDestroy(hi);
             for (cudaStream_t x : sv->streams) cudaStreamDestroy(x);
+            for (cudaStream_t x : sv->streams_lo) cudaStreamDestroy(x);
             delete sv;
             return fail(QCD_ERR_CUDA, "server_create: cudaStreamCreate failed");
         }
-        sv->streams.push_back(st);
+        sv->streams.push_back(hi);
+        sv->streams_lo.push_back(lo);
     }
     for (int s = 0; s < cfg->slots; ++s) sv->workers.emplace_back(worker, sv, s);
     *out = sv;
@@ -282,6 +294,7 @@ void qcd_server_destroy(qcd_server *sv)
     for (auto &m : sv->slot_ctx)
         for (auto &kv : m) release(sv, kv.second);
     for (cudaStream_t s : sv->streams) cudaStreamDestroy(s);
+    for (cudaStream_t s : sv->streams_lo) cudaStreamDestroy(s);
     for (auto &kv : sv->jobs) delete kv.second;
     delete sv;
 }

@@ -36,7 +36,31 @@ struct OpCtx {
     double kappa, a;  // a = 2 kappa mu
     bool eo;
     const Reduction *red;  // scratch of the fused |Mhat p|^2 reduction
+    const double *coef;    // device table of the normal operator's epilogue coefficients (4 x 8), or nullptr
 };
+
+// Epilogue coefficients of the normal operator's hops (see apply_normal),
+// 8 doubles each (cy[2][2], cd[2][2]).
+CoefTable normal_op_table(const OpCtx &c)
+{
+    CoefTable t{};
+    auto put = [&](int k, const Coef &cy, const Coef &cd) {
+        memcpy(t.v + 8 * k, cy.c, 4 * sizeof(double));
+        memcpy(t.v + 8 * k + 4, cd.c, 4 * sizeof(double));
+    };
+    const Coef zero = coef_real(0.0);
+    if (c.eo) {
+        put(0, zero, coef_twist_inv(c.a));
+        put(1, coef_twist(c.a), coef_real(-c.kappa * c.kappa));
+        put(2, zero, coef_twist_inv(-c.a));
+        put(3, coef_twist(-c.a), coef_real(-c.kappa * c.kappa));
+    } else {
+        put(0, coef_twist(c.a), coef_real(-c.kappa));
+        put(1, coef_twist(-c.a), coef_real(-c.kappa));
+    }
+    t.n = 32;
+    return t;
+}
 
 // out = Mhat^dag Mhat in (eo) or M^dag M in (full).  t (odd half) and s
 // (even half, or full) are temporaries of the same precision.  With
@@ -57,6 +81,7 @@ cudaError_t apply_normal(const OpCtx &c, const GaugeView &U, int recon, const Fi
         h.plain = !tw;
         h.twisted = tw;
         h.cd = coef_twist_inv(c.a);
+        h.coef = c.coef;
         if ((e = hop(c.lat, U, recon, h, st)) != cudaSuccess) return e;
         // s = A in - kappa^2 D_eo t   (|s|^2 -> alpha)
         HopArgs h2{};
@@ -71,12 +96,14 @@ cudaError_t apply_normal(const OpCtx &c, const GaugeView &U, int recon, const Fi
         h2.cd = coef_real(-c.kappa * c.kappa);
         h2.reduce = reduce_alpha;
         h2.red = c.red;
+        h2.coef = c.coef ? c.coef + 8 : nullptr;
         if ((e = hop(c.lat, U, recon, h2, st)) != cudaSuccess) return e;
         // t = A^-dag D_oe^dag s
         HopArgs h3 = h;
         h3.in = &s;
         h3.dagger = 1;
         h3.cd = coef_twist_inv(-c.a);
+        h3.coef = c.coef ? c.coef + 16 : nullptr;
         if ((e = hop(c.lat, U, recon, h3, st)) != cudaSuccess) return e;
         // out = A^dag s - kappa^2 D_eo^dag t
         HopArgs h4 = h2;
@@ -86,6 +113,7 @@ cudaError_t apply_normal(const OpCtx &c, const GaugeView &U, int recon, const Fi
         h4.dagger = 1;
         h4.cy = coef_twist(-c.a);
         h4.reduce = false;
+        h4.coef = c.coef ? c.coef + 24 : nullptr;
         return hop(c.lat, U, recon, h4, st);
     }
     // s = M in = A in - kappa D in  (|s|^2 -> alpha)
@@ -101,6 +129,7 @@ cudaError_t apply_normal(const OpCtx &c, const GaugeView &U, int recon, const Fi
     h.cd = coef_real(-c.kappa);
     h.reduce = reduce_alpha;
     h.red = c.red;
+    h.coef = c.coef;
     if ((e = hop(c.lat, U, recon, h, st)) != cudaSuccess) return e;
     // out = M^dag s
     HopArgs h2 = h;
@@ -110,6 +139,7 @@ cudaError_t apply_normal(const OpCtx &c, const GaugeView &U, int recon, const Fi
     h2.dagger = 1;
     h2.cy = coef_twist(-c.a);
     h2.reduce = false;
+    h2.coef = c.coef ? c.coef + 8 : nullptr;
     return hop(c.lat, U, recon, h2, st);
 }
 
@@ -228,8 +258,8 @@ cudaError_t cg_eager(const qcd_lattice *lat, const CgFields &f, cudaStream_t s)
 qcd_status cg_graph(const qcd_lattice *lat, const CgFields &f, cudaGraphExec_t *out)
 {
     char key[512];
-    snprintf(key, sizeof(key), "%d|%a|%a|%d|%d|%d|%p|%p|%p|%p|%p|%p|%p|%p|%p|%p|%p|%p|%p|%p|%d|%d", (int)f.c.eo,
-             f.c.kappa, f.c.a, (int)f.mixed, f.rh_recon, f.rs_recon, f.Uh.data, f.Us.data, f.rhs.hv[0].data,
+    snprintf(key, sizeof(key), "%d|%d|%p|%d|%d|%d|%p|%p|%p|%p|%p|%p|%p|%p|%p|%p|%p|%p|%p|%p|%d|%d", (int)f.c.eo,
+             (int)(f.c.a != 0.0), (const void *)f.c.coef, (int)f.mixed, f.rh_recon, f.rs_recon, f.Uh.data, f.Us.data, f.rhs.hv[0].data,
              f.xh.hv[0].data, f.xh.hv[1].data, f.rh.hv[0].data, f.qh.hv[0].data, f.th.hv[0].data, f.sh.hv[0].data,
              f.rs.hv[0].data, f.ps.hv[0].data, f.qs.hv[0].data, f.ts.hv[0].data, f.ss.hv[0].data, f.xs.hv[0].data,
              (void *)f.state, f.rs.prec, f.rhs.nh);
@@ -395,7 +425,7 @@ qcd_status qcd::solve_impl(const qcd_gauge *g, qcd_spinor *const *x, const qcd_s
     int L = 0;
     while ((1 << L) < nrhs) ++L;
     const int N = 1 << L;
-    OpCtx c{lat, prm->kappa, 2.0 * prm->kappa * prm->mu, prm->eo != 0, nullptr};
+    OpCtx c{lat, prm->kappa, 2.0 * prm->kappa * prm->mu, prm->eo != 0, nullptr, nullptr};
     const bool tw = c.a != 0.0;
     const int nh = c.eo ? 1 : 2;
 
@@ -420,6 +450,12 @@ qcd_status qcd::solve_impl(const qcd_gauge *g, qcd_spinor *const *x, const qcd_s
         if (!red.partials) return fail(QCD_ERR_OOM, "solve_cg: workspace");
     }
     c.red = &red;
+    // the normal operator's coefficients live in a device table, so the
+    // cached CG graph does not depend on kappa and mu
+    double *coef = static_cast<double *>(workspace(lat, "cg_coef", 64 * sizeof(double)));
+    if (!coef) return fail(QCD_ERR_OOM, "solve_cg: workspace");
+    c.coef = coef;
+    QCD_TRY(launch_set_table(coef, normal_op_table(c), s), "solve_cg: coefficients");
 
     // FP64 fields
     FieldView rhs = c.eo ? ws_field(lat, "cg_rhs", 1, QCD_PREC_F64, L) : bf;
