@@ -42,6 +42,10 @@ WORKLOAD = "24^3x8"
 TOL = 1e-10
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x FP64 FMA/clk x 2 flop x max clock
 HBM_FALLBACK_GBS = 6800.0
+# DRAM bytes (read + write) of one FP64 D_eo launch at 24^3 x 8 from an ncu
+# capture of the current kernel (profiles/dslash_f64_r18_24x24x24x8.md);
+# set to None when the kernel changes.
+TRAFFIC_F64_D_24 = 76.87e6
 
 
 def peaks():
@@ -515,7 +519,9 @@ def main():
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu", "kernel": "dslash FP64 (D_eo/D_oe with fused epilogues) in the CG",
                      "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS if achieved else None, "traffic": None,
+                     "frac": achieved / FP64_PEAK_TFLOPS if achieved else None, "traffic": TRAFFIC_F64_D_24,
+                     "traffic_note": "ncu dram read+write bytes per plain D_eo launch at 24^3x8 (cold cache); "
+                                     "algorithmic 84.93 MB",
                      "launches": d["launches"], "avg_us": d["ms"] / max(d["launches"], 1) * 1e3,
                      "achieved_GB_s": d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else None,
                      "hbm_peak_GB_s": hbm,
