@@ -52,6 +52,7 @@ def _load():
         lib.oracle_apply_m.argtypes = [p, d, p, d, d, p, p, i]
         lib.oracle_dhop_eo.argtypes = [p, d, p, i, p, p, i]
         lib.oracle_dhop_sites.argtypes = [p, d, p, p, p, ctypes.c_long, p, i]
+        lib.oracle_dks.argtypes = [p, d, p, p, p]
         lib.oracle_apply_mhat.argtypes = [p, d, p, d, d, p, p, i]
         lib.oracle_twist.argtypes = [p, p, ctypes.c_long, d, i]
         for f in (lib.oracle_solve_mdagm, lib.oracle_solve_m, lib.oracle_solve_eo):
@@ -104,6 +105,15 @@ def apply_m(U, psi, kappa, mu=0.0, t_bc=-1.0, dagger=False):
     out = np.empty_like(psi)
     _load().oracle_apply_m(_dims(U), float(t_bc), pu, float(kappa), float(mu), pp,
                            out.ctypes.data_as(ctypes.c_void_p), int(dagger))
+    return out
+
+
+def dks(U, chi, t_bc=-1.0):
+    """Staggered derivative D_KS chi on the full lattice; chi[t,z,y,x,3] complex."""
+    U, pu = _c(U)
+    chi, pc = _c(chi)
+    out = np.empty_like(chi)
+    _load().oracle_dks(_dims(U), float(t_bc), pu, pc, out.ctypes.data_as(ctypes.c_void_p))
     return out
 
 
