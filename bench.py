@@ -358,6 +358,38 @@ def serving_block(qcd, torch, n_requests=2000, rate=30.0, slots=8, seed=1006):
     return out
 
 
+def dslash_ks_sweep(qcd, torch, flush, hbm, reps=20):
+    """Staggered D_KS (the paper's Fig. 4 kernel) on the five volumes, cold L2:
+    GB/s on the compulsory bytes (8 links + input + output vector per site)."""
+    from paper_1411_5219_gb300 import synthetic as syn
+    fmts = [("f64", 18, 8 * 144 + 2 * 48), ("f32", 12, 8 * 48 + 2 * 24), ("f16", 12, 8 * 24 + 2 * 16)]
+    out = {}
+    for dims in syn.SWEEP_VOLUMES:
+        lat = qcd.Lattice(dims, -1)
+        U = syn.gauge_field(dims, 0.2, 1002)
+        lx, ly, lz, lt = dims
+        chi = syn.gaussian_complex(7, syn.STREAM_AUX, (lt, lz, ly, lx, 3))
+        par = syn.parity_of_sites(dims).reshape(-1)
+        half_odd = np.ascontiguousarray(chi.reshape(-1, 3)[par == 1])
+        h = lat.volume // 2
+        row = {}
+        for prec, recon, bps in fmts:
+            g = qcd.Gauge(lat, "f64", recon)
+            g.upload(U)
+            si, so = qcd.Spinor(lat, "odd", prec, ks=True), qcd.Spinor(lat, "even", prec, ks=True)
+            si.upload(half_odd)
+            fn = lambda: qcd.apply_dslash_ks(g, so, si)  # noqa: E731
+            for _ in range(3):
+                fn()
+            t = float(np.median(timed_steps(torch, fn, reps, flush)))
+            row[f"{prec}_r{recon}"] = {"us": round(t * 1e6, 2), "GB_s": round(h * bps / t / 1e9, 1),
+                                       "frac_hbm": round(h * bps / t / 1e9 / hbm, 3),
+                                       "GFLOP_s": round(h * 570 / t / 1e9, 1)}
+            del g
+        out["x".join(map(str, dims))] = row
+    return out
+
+
 def cpu_oracle_sample(target_s=15.0):
     """Time FP64 oracle CG iterations on this host's cores (bounded sample)."""
     import oracle
@@ -590,6 +622,7 @@ def main():
         line["full_4x4_normal_solves_s"] = args.steps / float(np.sum(t4))
         del p4
         line["serving"] = serving_block(qcd, torch, n_requests=args.serve_requests)
+        line["dslash_ks_sweep"] = dslash_ks_sweep(qcd, torch, flush, hbm)
         line["dslash_sweep"] = dslash_sweep(qcd, torch, flush, hbm)
         line["dslash_sweep_note"] = (f"cold L2 (flushed before each launch); GB/s on compulsory bytes per "
                                      f"output site; frac of {hbm_kind} HBM {hbm} GB/s")

@@ -128,6 +128,13 @@ void qcd_gauge_destroy(qcd_gauge *g);
  * parity (EVEN/ODD, V/2 sites) or on all sites (FULL = even half then odd
  * half).  F16 keeps one FP32 scale per site.  Errors: INVALID_ARG; OOM. */
 qcd_status qcd_spinor_create(const qcd_lattice *lat, qcd_parity parity, qcd_prec prec, qcd_spinor **out);
+/* A staggered field (one colour vector, 3 complex per site), the field of
+ * the paper's second Dirac operator D_KS (Sec. 1, Sec. 6), in F64, F32, F16
+ * (with FP32 per-site scale) or BF16.  Host layout [t][z][y][x][colour]
+ * (FULL) or [lex/2][colour] (EVEN/ODD); qcd_spinor_upload/download and
+ * qcd_spinor_destroy accept it, the Wilson operators, norms, conversions
+ * and solvers reject it (INVALID_ARG).  Errors: INVALID_ARG; OOM. */
+qcd_status qcd_spinor_create_ks(const qcd_lattice *lat, qcd_parity parity, qcd_prec prec, qcd_spinor **out);
 /* Device bytes of such a field: *data_bytes for the planes, *norm_bytes
  * for the F16 per-site scales (0 otherwise). */
 qcd_status qcd_spinor_bytes(const qcd_lattice *lat, qcd_parity parity, qcd_prec prec, size_t *data_bytes,
@@ -191,6 +198,16 @@ qcd_status qcd_norm2_noalloc(const double *x_device, size_t n, double *result_de
  * copy in that precision and with the gauge field's recon is used.
  * Errors: INVALID_ARG (parities, lattices, precisions); CUDA. */
 qcd_status qcd_apply_dslash(const qcd_gauge *g, qcd_spinor *out, const qcd_spinor *in, int dagger, void *stream);
+
+/* out = D_KS in, the staggered derivative (Sec. 1, Sec. 6):
+ *   (D_KS chi)(x) = sum_mu eta_mu(x) [U_mu(x) chi(x+mu) - U_mu(x-mu)^dagger chi(x-mu)],
+ *   eta_x = 1, eta_y = (-1)^x, eta_z = (-1)^(x+y), eta_t = (-1)^(x+y+z),
+ * with t_bc on hops that wrap in time; 570 flop per site, as the paper
+ * counts (no factor 1/2).  Staggered fields of one precision; parities as
+ * for qcd_apply_dslash (D_KS connects even and odd sites only).  The gauge
+ * field's copy in that precision and recon is used.  D_KS^dagger = -D_KS.
+ * Errors: INVALID_ARG; CUDA. */
+qcd_status qcd_apply_dslash_ks(const qcd_gauge *g, qcd_spinor *out, const qcd_spinor *in, void *stream);
 
 /* eo = 0: out = M in on FULL fields, M = A - kappa D_hop (Wilson, Sec. 3;
  *         twisted mass for mu != 0, Sec. 3).

@@ -701,6 +701,71 @@ qcd_status qcd_spinor_create(const qcd_lattice *lat, qcd_parity parity, qcd_prec
     return QCD_OK;
 }
 
+qcd_status qcd_spinor_create_ks(const qcd_lattice *lat, qcd_parity parity, qcd_prec prec, qcd_spinor **out)
+{
+    if (!lat || !out) return fail(QCD_ERR_INVALID_ARG, "spinor_create_ks: NULL argument");
+    *out = nullptr;
+    if (prec < QCD_PREC_F64 || prec > QCD_PREC_BF16 || parity < 0 || parity > 2)
+        return fail(QCD_ERR_INVALID_ARG, "spinor_create_ks: bad prec/parity");
+    qcd_spinor *s = new (std::nothrow) qcd_spinor();
+    if (!s) return fail(QCD_ERR_OOM, "spinor_create_ks: host allocation");
+    s->lat = lat;
+    s->parity = parity;
+    s->prec = prec;
+    s->ks = true;
+    const size_t elem = prec == QCD_PREC_F64 ? 16 : prec == QCD_PREC_F32 ? 8 : 4;
+    s->half_data_bytes = 3 * elem * lat->stride;
+    s->half_norm_bytes = prec == QCD_PREC_F16 ? (size_t)4 * lat->stride : 0;
+    const int nh = parity == QCD_PARITY_FULL ? 2 : 1;
+    DeviceLock dl(device_mutex());
+    cudaError_t e = cudaMalloc(&s->data, nh * s->half_data_bytes);
+    if (e == cudaSuccess && s->half_norm_bytes) e = cudaMalloc(reinterpret_cast<void **>(&s->norm), nh * s->half_norm_bytes);
+    if (e == cudaSuccess) e = cudaMemset(s->data, 0, nh * s->half_data_bytes);
+    if (e == cudaSuccess && s->norm) e = cudaMemset(s->norm, 0, nh * s->half_norm_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(s->data);
+        cudaFree(s->norm);
+        delete s;
+        return fail(QCD_ERR_OOM, "spinor_create_ks: cudaMalloc failed");
+    }
+    *out = s;
+    return QCD_OK;
+}
+
+qcd_status qcd_apply_dslash_ks(const qcd_gauge *g, qcd_spinor *out, const qcd_spinor *in, void *stream)
+{
+    if (!g || !out || !in) return fail(QCD_ERR_INVALID_ARG, "apply_dslash_ks: NULL argument");
+    if (!out->ks || !in->ks) return fail(QCD_ERR_INVALID_ARG, "apply_dslash_ks: fields must be staggered");
+    if (out->lat != g->lat || in->lat != g->lat) return fail(QCD_ERR_INVALID_ARG, "apply_dslash_ks: lattices differ");
+    if (out->prec != in->prec) return fail(QCD_ERR_INVALID_ARG, "apply_dslash_ks: precisions differ");
+    if (out->data == in->data) return fail(QCD_ERR_INVALID_ARG, "apply_dslash_ks: out aliases in");
+    const bool both = out->parity == QCD_PARITY_FULL && in->parity == QCD_PARITY_FULL;
+    if (!both && !(out->parity != QCD_PARITY_FULL && in->parity == 1 - out->parity))
+        return fail(QCD_ERR_INVALID_ARG, "apply_dslash_ks: parities must be (EVEN, ODD), (ODD, EVEN) or (FULL, FULL)");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    qcd_status st;
+    GaugeView U = gauge_view(g, out->prec, g->recon, s, &st);
+    if (st != QCD_OK) return st;
+    const FieldView fo = view_of(out), fi = view_of(in);
+    KsLaunch a;
+    memset(&a, 0, sizeof(a));
+    a.g = g->lat->geom;
+    a.both = both ? 1 : 0;
+    a.out_parity = both ? 0 : out->parity;
+    a.U = U;
+    if (both) {
+        for (int p = 0; p < 2; ++p) {
+            a.out[p] = fo.hv[p];
+            a.in[p] = fi.hv[1 - p];
+        }
+    } else {
+        a.out[a.out_parity] = fo.hv[0];
+        a.in[a.out_parity] = fi.hv[0];
+    }
+    return check_cuda(launch_dslash_ks(out->prec, g->recon, a, s), "apply_dslash_ks");
+}
+
 qcd_status qcd_spinor_wrap_device(const qcd_lattice *lat, qcd_parity parity, qcd_prec prec, void *data, void *norm,
                                   qcd_spinor **out)
 {
@@ -736,7 +801,14 @@ qcd_status qcd_spinor_upload(qcd_spinor *s, const double *host, void *stream)
     if (!s || !host) return fail(QCD_ERR_INVALID_ARG, "spinor_upload: NULL argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int nh = s->parity == QCD_PARITY_FULL ? 2 : 1;
-    const size_t bytes = (size_t)nh * s->lat->h * 192;
+    const size_t bytes = (size_t)nh * s->lat->h * (s->ks ? 48 : 192);
+    if (s->ks) {
+        void *stage = workspace(s->lat, "staging", bytes);
+        if (!stage) return fail(QCD_ERR_OOM, "spinor_upload: staging");
+        cudaError_t e = cudaMemcpyAsync(stage, host, bytes, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = launch_ks_pack(view_of(s), s->parity, static_cast<const double2 *>(stage), s->lat->geom, st);
+        return check_cuda(e, "spinor_upload");
+    }
     void *stage = workspace(s->lat, "staging", bytes);
     if (!stage) return fail(QCD_ERR_OOM, "spinor_upload: staging");
     cudaError_t e = cudaMemcpyAsync(stage, host, bytes, cudaMemcpyHostToDevice, st);
@@ -750,7 +822,14 @@ qcd_status qcd_spinor_download(const qcd_spinor *s, double *host, void *stream)
     if (!s || !host) return fail(QCD_ERR_INVALID_ARG, "spinor_download: NULL argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int nh = s->parity == QCD_PARITY_FULL ? 2 : 1;
-    const size_t bytes = (size_t)nh * s->lat->h * 192;
+    const size_t bytes = (size_t)nh * s->lat->h * (s->ks ? 48 : 192);
+    if (s->ks) {
+        void *stage = workspace(s->lat, "staging", bytes);
+        if (!stage) return fail(QCD_ERR_OOM, "spinor_download: staging");
+        cudaError_t e = launch_ks_unpack(static_cast<double2 *>(stage), view_of(s), s->parity, s->lat->geom, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(host, stage, bytes, cudaMemcpyDeviceToHost, st);
+        return check_cuda(e, "spinor_download");
+    }
     void *stage = workspace(s->lat, "staging", bytes);
     if (!stage) return fail(QCD_ERR_OOM, "spinor_download: staging");
     cudaError_t e = launch_spinor_unpack(static_cast<double2 *>(stage), view_of(s), s->parity, s->lat->geom, st);
@@ -761,6 +840,7 @@ qcd_status qcd_spinor_download(const qcd_spinor *s, double *host, void *stream)
 qcd_status qcd_spinor_zero(qcd_spinor *s, void *stream)
 {
     if (!s) return fail(QCD_ERR_INVALID_ARG, "spinor_zero: NULL argument");
+    if (s->ks) return fail(QCD_ERR_INVALID_ARG, "spinor_zero: not defined for staggered fields");
     return check_cuda(launch_zero(view_of(s), static_cast<cudaStream_t>(stream)), "spinor_zero");
 }
 
@@ -769,12 +849,14 @@ qcd_status qcd_spinor_convert(qcd_spinor *dst, const qcd_spinor *src, void *stre
     if (!dst || !src) return fail(QCD_ERR_INVALID_ARG, "spinor_convert: NULL argument");
     if (dst->lat != src->lat || dst->parity != src->parity)
         return fail(QCD_ERR_INVALID_ARG, "spinor_convert: lattice or parity differ");
+    if (dst->ks || src->ks) return fail(QCD_ERR_INVALID_ARG, "spinor_convert: not defined for staggered fields");
     return check_cuda(launch_convert(view_of(dst), view_of(src), static_cast<cudaStream_t>(stream)), "spinor_convert");
 }
 
 qcd_status qcd_spinor_norm2(const qcd_spinor *s, double *result_device, void *stream)
 {
     if (!s || !result_device) return fail(QCD_ERR_INVALID_ARG, "spinor_norm2: NULL argument");
+    if (s->ks) return fail(QCD_ERR_INVALID_ARG, "spinor_norm2: not defined for staggered fields");
     return check_cuda(launch_norm2(view_of(s), reduction_of(s->lat), FIN_STORE, s->lat->state, result_device,
                                    static_cast<cudaStream_t>(stream)),
                       "spinor_norm2");
@@ -785,6 +867,7 @@ qcd_status qcd_apply_dslash(const qcd_gauge *g, qcd_spinor *out, const qcd_spino
     if (!g || !out || !in) return fail(QCD_ERR_INVALID_ARG, "apply_dslash: NULL argument");
     if (out->lat != g->lat || in->lat != g->lat) return fail(QCD_ERR_INVALID_ARG, "apply_dslash: lattices differ");
     if (out->prec != in->prec) return fail(QCD_ERR_INVALID_ARG, "apply_dslash: precisions differ");
+    if (out->ks || in->ks) return fail(QCD_ERR_INVALID_ARG, "apply_dslash: staggered fields need qcd_apply_dslash_ks");
     if (out == in || out->data == in->data) return fail(QCD_ERR_INVALID_ARG, "apply_dslash: out aliases in");
     const bool both = out->parity == QCD_PARITY_FULL && in->parity == QCD_PARITY_FULL;
     if (!both && !(out->parity != QCD_PARITY_FULL && in->parity == 1 - out->parity))
@@ -854,6 +937,7 @@ qcd_status qcd_apply_M(const qcd_gauge *g, qcd_spinor *out, const qcd_spinor *in
     if (!g || !out || !in) return fail(QCD_ERR_INVALID_ARG, "apply_M: NULL argument");
     if (out->lat != g->lat || in->lat != g->lat) return fail(QCD_ERR_INVALID_ARG, "apply_M: lattices differ");
     if (out->prec != in->prec) return fail(QCD_ERR_INVALID_ARG, "apply_M: precisions differ");
+    if (out->ks || in->ks) return fail(QCD_ERR_INVALID_ARG, "apply_M: not defined for staggered fields");
     if (out == in || out->data == in->data) return fail(QCD_ERR_INVALID_ARG, "apply_M: out aliases in");
     if (eo && (out->parity != QCD_PARITY_EVEN || in->parity != QCD_PARITY_EVEN))
         return fail(QCD_ERR_INVALID_ARG, "apply_M: eo = 1 needs EVEN fields");

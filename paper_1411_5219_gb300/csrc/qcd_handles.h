@@ -56,6 +56,7 @@ struct qcd_spinor {
     size_t half_data_bytes = 0;  // bytes of one half field's planes
     size_t half_norm_bytes = 0;
     bool owns = true;
+    bool ks = false;  // staggered field: 3 complex per site
 };
 
 namespace qcd {

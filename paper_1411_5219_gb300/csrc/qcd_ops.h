@@ -63,6 +63,19 @@ cudaError_t launch_cg_ctrl_loop(CgState *st, cudaGraphConditionalHandle h, cudaS
 // precision and halves: to_batch = 1 copies plain -> batched[rhs].
 cudaError_t launch_batch_copy(const FieldView &batched, const FieldView &plain, int rhs, int to_batch, cudaStream_t s);
 
+// Staggered hopping term (csrc/staggered.cu).  in/out indexed by output
+// parity as for DslashLaunch; staggered fields hold 3 complex per site.
+struct KsLaunch {
+    Geom g;
+    int out_parity;
+    int both;
+    GaugeView U;
+    SpinorView in[2], out[2];
+};
+cudaError_t launch_dslash_ks(int prec, int recon, const KsLaunch &a, cudaStream_t s);
+cudaError_t launch_ks_pack(const FieldView &f, int parity, const double2 *aos, const Geom &g, cudaStream_t s);
+cudaError_t launch_ks_unpack(double2 *aos, const FieldView &f, int parity, const Geom &g, cudaStream_t s);
+
 // Layout conversion between the host AoS form (FP64, lexicographic) and the
 // device SoA form.
 cudaError_t launch_gauge_pack(const GaugeView &dst, int prec, int recon, const double2 *aos, const Geom &g,

@@ -399,6 +399,7 @@ qcd_status qcd::solve_impl(const qcd_gauge *g, qcd_spinor *const *x, const qcd_s
             b[k]->prec != QCD_PREC_F64)
             return fail(QCD_ERR_INVALID_ARG, "solve_cg: x and b must be FULL F64 fields");
         if (x[k]->data == b[k]->data) return fail(QCD_ERR_INVALID_ARG, "solve_cg: x aliases b");
+        if (x[k]->ks || b[k]->ks) return fail(QCD_ERR_INVALID_ARG, "solve_cg: staggered fields are not solved here");
     }
     if (g->prec != QCD_PREC_F64) return fail(QCD_ERR_INVALID_ARG, "solve_cg: the gauge field must be F64");
     if (!(prm->tol > 0.0) || prm->maxiter < 1 || !std::isfinite(prm->kappa) || !std::isfinite(prm->mu))

@@ -73,6 +73,8 @@ _SIGS = {
     "qcd_gauge_prepare": (_i, [_p, _i, _i, _p]),
     "qcd_gauge_destroy": (None, [_p]),
     "qcd_spinor_create": (_i, [_p, _i, _i, ctypes.POINTER(_p)]),
+    "qcd_spinor_create_ks": (_i, [_p, _i, _i, ctypes.POINTER(_p)]),
+    "qcd_apply_dslash_ks": (_i, [_p, _p, _p, _p]),
     "qcd_spinor_bytes": (_i, [_p, _i, _i, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
     "qcd_spinor_wrap_device": (_i, [_p, _i, _i, _p, _p, ctypes.POINTER(_p)]),
     "qcd_spinor_upload": (_i, [_p, _p, _p]),
@@ -222,11 +224,15 @@ class Spinor:
     With ``torch_alloc=True`` the device memory is a torch tensor wrapped
     through qcd_spinor_wrap_device (torch's allocator owns it)."""
 
-    def __init__(self, lat: Lattice, parity: str = "full", prec: str = "f64", torch_alloc: bool = False):
-        self.lat, self.parity, self.prec = lat, parity, prec
+    def __init__(self, lat: Lattice, parity: str = "full", prec: str = "f64", torch_alloc: bool = False,
+                 ks: bool = False):
+        self.lat, self.parity, self.prec, self.ks = lat, parity, prec, bool(ks)
         h = _p()
         self._buffers = None
-        if torch_alloc:
+        if ks:
+            _check(lib().qcd_spinor_create_ks(lat.handle, PARITY[parity], PREC[prec], ctypes.byref(h)),
+                   "qcd_spinor_create_ks")
+        elif torch_alloc:
             import torch
             nd, nn = ctypes.c_size_t(), ctypes.c_size_t()
             _check(lib().qcd_spinor_bytes(lat.handle, PARITY[parity], PREC[prec], ctypes.byref(nd),
@@ -248,9 +254,10 @@ class Spinor:
     @property
     def host_shape(self):
         lx, ly, lz, lt = self.lat.dims
+        inner = (3,) if self.ks else (4, 3)
         if self.parity == "full":
-            return (lt, lz, ly, lx, 4, 3)
-        return (self.lat.volume // 2, 4, 3)
+            return (lt, lz, ly, lx) + inner
+        return (self.lat.volume // 2,) + inner
 
     def upload(self, psi, stream=None):
         if tuple(psi.shape) != self.host_shape:
@@ -291,6 +298,11 @@ def apply_dslash(gauge: Gauge, out: Spinor, inp: Spinor, dagger: bool = False, s
     """out = D_hop inp (parity block or full lattice); see qcd_apply_dslash."""
     _check(lib().qcd_apply_dslash(gauge.handle, out.handle, inp.handle, int(bool(dagger)), _stream(stream)),
            "qcd_apply_dslash")
+
+
+def apply_dslash_ks(gauge: Gauge, out: Spinor, inp: Spinor, stream=None):
+    """out = D_KS inp, the staggered derivative (qcd_apply_dslash_ks)."""
+    _check(lib().qcd_apply_dslash_ks(gauge.handle, out.handle, inp.handle, _stream(stream)), "qcd_apply_dslash_ks")
 
 
 def apply_M(gauge: Gauge, out: Spinor, inp: Spinor, kappa: float, mu: float = 0.0, eo: bool = False,

@@ -626,3 +626,43 @@ def test_server_overlap_and_memory_budget(q):
     assert e.value.status == 2
     sv.close()
     big.close()
+
+
+# ------------------------------------------------------- staggered D_KS
+
+def ks_half(chi, parity):
+    dims = chi.shape[:4][::-1]
+    p = syn.parity_of_sites(dims).reshape(-1)
+    return np.ascontiguousarray(chi.reshape(-1, 3)[p == parity])
+
+
+@pytest.mark.parametrize("dims", DIMS)
+@pytest.mark.parametrize("prec,recon", [("f64", 18), ("f64", 12), ("f32", 12), ("f16", 12), ("bf16", 12)])
+def test_dslash_ks_matches_oracle(q, dims, prec, recon):
+    lat, U, g = gauge(q, dims, recon=recon)
+    lx, ly, lz, lt = dims
+    chi = syn.gaussian_complex(60, syn.STREAM_AUX, (lt, lz, ly, lx, 3))
+    for out_par in (0, 1):
+        src = chi * (syn.parity_of_sites(dims) == 1 - out_par)[..., None]
+        want = ks_half(oracle.dks(U, src), out_par)
+        si = q.Spinor(lat, "odd" if out_par == 0 else "even", prec, ks=True)
+        so = q.Spinor(lat, "even" if out_par == 0 else "odd", prec, ks=True)
+        si.upload(ks_half(chi, 1 - out_par))
+        q.apply_dslash_ks(g, so, si)
+        assert F.rel_err(so.download(), want) <= tol_of(prec), (prec, recon)
+
+
+def test_dslash_ks_full_point_source_and_roundtrip(q):
+    dims = (6, 4, 4, 4)
+    lat, U, g = gauge(q, dims)
+    chi = np.zeros((4, 4, 4, 6, 3), dtype=complex)
+    chi[3, 2, 0, 3, 1] = 1.0
+    si, so = q.Spinor(lat, "full", "f64", ks=True), q.Spinor(lat, "full", "f64", ks=True)
+    si.upload(chi)
+    assert np.array_equal(si.download(), chi)
+    q.apply_dslash_ks(g, so, si)
+    out = so.download()
+    assert len(np.argwhere(np.abs(out).sum(axis=4) > 0)) == 8
+    assert F.rel_err(out, oracle.dks(U, chi)) <= 1e-13
+    with pytest.raises(q.QcdError):
+        q.apply_dslash(g, so, si)  # Wilson operator on staggered fields
