@@ -57,6 +57,19 @@ def peaks():
         return HBM_FALLBACK_GBS, "fallback"
 
 
+def max_over_ranks(value: float, world_size: int) -> float:
+    """The largest value over all ranks (the timed region's max-over-ranks
+    rule); identity for one rank.  Works with the nccl and gloo backends."""
+    if world_size == 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -522,11 +535,7 @@ def main():
     if ws > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    total = float(np.sum(ts))
-    if ws > 1:
-        t = torch.tensor([total], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total = float(t.item())
+    total = max_over_ranks(float(np.sum(ts)), ws)
     value = ws * args.steps / total
     iters = [s["iterations"] for s in stats]
     resid = max(s["true_rel_residual"] for s in stats)
