@@ -462,20 +462,24 @@ def run_reference(args):
 
 
 def dslash_only(args):
-    """Launch D_eo `reps` times on one volume/format (for ncu), print timings."""
+    """Launch D_eo `reps` times on one volume (for ncu); PREC may list several
+    formats (f16,bf16); prints the event-timed durations per format."""
     import torch
     from paper_1411_5219_gb300 import qcd, synthetic as syn
     dims = tuple(int(v) for v in args.dslash[0].split("x"))
-    prec, recon = args.dslash[1], int(args.dslash[2])
+    precs, recon = args.dslash[1].split(","), int(args.dslash[2])
     lat = qcd.Lattice(dims, -1)
     g = qcd.Gauge(lat, "f64", recon)
-    g.upload(syn.gauge_field(dims, 0.2, 1002))
-    g.prepare(prec, recon)
-    si, so = qcd.Spinor(lat, "odd", prec), qcd.Spinor(lat, "even", prec)
-    si.upload(syn.to_half(syn.gaussian_spinor(dims, 5), 1))
+    g.upload(syn.gauge_field(dims, 0.2, 1002, device="cuda"))
+    psi = syn.to_half(syn.gaussian_spinor(dims, 5), 1)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    ts = timed_steps(torch, lambda: qcd.apply_dslash(g, so, si), args.reps, flush)
-    print(json.dumps({"dslash": args.dslash, "us": [round(t * 1e6, 2) for t in ts]}))
+    for prec in precs:
+        g.prepare(prec, recon)
+        si, so = qcd.Spinor(lat, "odd", prec), qcd.Spinor(lat, "even", prec)
+        si.upload(psi)
+        ts = timed_steps(torch, lambda: qcd.apply_dslash(g, so, si), args.reps, flush)
+        print(json.dumps({"dslash": [args.dslash[0], prec, recon], "us": [round(t * 1e6, 2) for t in ts],
+                          "median_us": round(float(np.median(ts)) * 1e6, 2)}), flush=True)
     return 0
 
 

@@ -62,7 +62,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             print(r.stderr, file=sys.stderr)
         return obj
 
-    srcs = sources()
+    # the hopping-kernel units take longest: start them first
+    srcs = sorted(sources(), key=lambda f: (not os.path.basename(f).startswith("dslash"), f))
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + f".{os.getpid()}.tmp"
