@@ -190,14 +190,15 @@ def timed_steps(torch, fn, k, flush):
 def dslash_sweep(qcd, torch, flush, hbm, reps=20):
     from paper_1411_5219_gb300 import synthetic as syn
     out = {}
-    fmts = [("f64", 18, 1536), ("f64", 12, 1152), ("f32", 12, 576), ("f16", 12, 296), ("bf16", 12, 288)]
+    fmts = [("f64", 18, 1536), ("f64", 12, 1152), ("f32", 12, 576), ("f16", 12, 296), ("bf16", 12, 288),
+            ("f64", 8, 896), ("f32", 8, 448), ("f16", 8, 232), ("bf16", 8, 224)]
     for dims in syn.SWEEP_VOLUMES:
         lat = qcd.Lattice(dims, -1)
         U = syn.gauge_field(dims, 0.2, 1002)
         psi = syn.gaussian_spinor(dims, 5)
         h = lat.volume // 2
         row = {}
-        for recon in (18, 12):
+        for recon in (18, 12, 8):
             g = qcd.Gauge(lat, "f64", recon)
             g.upload(U)
             for prec, rc, bps in fmts:

@@ -74,9 +74,17 @@ typedef int qcd_status;
  * in double precision (Sec. 4); DF64 is this library's way to do so on
  * GB300 and is always labelled as such. */
 typedef enum { QCD_PREC_F64 = 0, QCD_PREC_F32 = 1, QCD_PREC_F16 = 2, QCD_PREC_BF16 = 3, QCD_PREC_DF64 = 4 } qcd_prec;
-/* Link storage: 18 reals (full matrix) or 12 (rows 0 and 1; row 2 is
- * rebuilt as conj(row0 x row1), exact for SU(3)). */
-typedef enum { QCD_RECON_18 = 18, QCD_RECON_12 = 12 } qcd_recon;
+/* Link storage: 18 reals (full matrix), 12 (rows 0 and 1; row 2 is
+ * rebuilt as conj(row0 x row1), exact for SU(3)) or 8.  Reconstruct-8 is
+ * pivoted for links near the identity: with W = U with its columns
+ * reversed, it stores W_00, W_01, W_10 and tan(arg/2) of W_02 = U_00 and
+ * W_20 = U_22; the two magnitudes follow from unit norms, the rest from
+ * unitarity and det U = 1, dividing by |W_01|^2 + |W_02|^2 (close to 1 when
+ * the diagonal dominates).  Every field written in this form is checked
+ * against its FP64 source (which synchronises the stream) and refused with
+ * INVALID_ARG when an entry is off by more than 1e-13 (F64), 32 u (F32) or
+ * 4 u (F16, BF16), u the unit roundoff; DF64 takes 18 only. */
+typedef enum { QCD_RECON_18 = 18, QCD_RECON_12 = 12, QCD_RECON_8 = 8 } qcd_recon;
 typedef enum { QCD_PARITY_EVEN = 0, QCD_PARITY_ODD = 1, QCD_PARITY_FULL = 2 } qcd_parity;
 
 typedef struct qcd_lattice qcd_lattice;
@@ -113,12 +121,15 @@ void qcd_lattice_destroy(qcd_lattice *lat);
  * first use by a Dslash of that precision.  Errors: INVALID_ARG; OOM. */
 qcd_status qcd_gauge_create(const qcd_lattice *lat, qcd_prec prec, qcd_recon recon, qcd_gauge **out);
 /* Copy a host gauge field (host layout above, 4*V*9 complex doubles) to
- * the device and convert it; drops derived copies.  Recon-12 assumes
- * SU(3) links.  Errors: INVALID_ARG (NULL); CUDA. */
+ * the device and convert it; drops derived copies.  Recon-12 and recon-8
+ * assume SU(3) links.  Errors: INVALID_ARG (NULL; recon-8 links out of
+ * reach, see qcd_recon); CUDA. */
 qcd_status qcd_gauge_upload(qcd_gauge *g, const double *host, void *stream);
 /* Build (if missing) the derived copy used by kernels of precision
  * `prec` with `recon` reals per link.  Optional: kernels build it on first
- * use.  Errors: INVALID_ARG; OOM. */
+ * use (a recon-8 copy must be built outside stream capture, since its
+ * check reads back to the host).  Errors: INVALID_ARG (also recon-8 links
+ * out of reach); OOM. */
 qcd_status qcd_gauge_prepare(qcd_gauge *g, qcd_prec prec, qcd_recon recon, void *stream);
 void qcd_gauge_destroy(qcd_gauge *g);
 

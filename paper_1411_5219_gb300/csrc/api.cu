@@ -95,11 +95,12 @@ size_t spinor_half_norm_bytes(int prec, int stride) { return prec == QCD_PREC_F1
 int gauge_planes(int prec, int recon)
 {
     if (prec == QCD_PREC_F64 || prec == QCD_PREC_DF64) return recon / 2;
+    if (recon == 8) return prec == QCD_PREC_F32 ? 2 : 1;
     return recon == 18 ? 9 : 3;
 }
 size_t gauge_plane_elem_bytes(int prec, int recon)
 {
-    if (prec == QCD_PREC_F64 || prec == QCD_PREC_DF64) return 16;
+    if (prec == QCD_PREC_F64 || prec == QCD_PREC_DF64 || recon == 8) return 16;
     if (prec == QCD_PREC_F32) return recon == 18 ? 8 : 16;
     return recon == 18 ? 4 : 8;
 }
@@ -109,7 +110,49 @@ size_t gauge_bytes(int prec, int recon, int stride)
 }
 
 static bool valid_prec(int p) { return p >= QCD_PREC_F64 && p <= QCD_PREC_DF64; }
-static bool valid_recon(int r) { return r == 18 || r == 12; }
+static bool valid_recon(int r) { return r == 18 || r == 12 || r == 8; }
+
+// Largest entry error a reconstruct-8 field may show against its FP64
+// source before it is refused: 4 units of the 16-bit roundoff (the storage
+// rounding itself is 0.5), 32 of FP32 (the FP32 rebuild costs ~7), and
+// 1e-13 in FP64.  Links far from the identity exceed these, since the
+// pivot assumes large diagonal entries.
+static double recon8_tolerance(int prec)
+{
+    switch (prec) {
+    case QCD_PREC_F64: return 1e-13;
+    case QCD_PREC_F32: return 32.0 * 0x1p-24;
+    case QCD_PREC_F16: return 4.0 * 0x1p-11;
+    case QCD_PREC_BF16: return 4.0 * 0x1p-8;
+    default: return 0.0;
+    }
+}
+
+static const char *prec_name(int prec)
+{
+    static const char *n[] = {"F64", "F32", "F16", "BF16", "DF64"};
+    return prec >= 0 && prec <= 4 ? n[prec] : "?";
+}
+
+// Validate a freshly written reconstruct-8 field (synchronises `s`).
+static qcd_status check_recon8(const GaugeView &dst, int prec, const double2 *aos, const GaugeView &src, int sprec,
+                               int srecon, const Geom &g, cudaStream_t s, const char *what)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+        return fail(QCD_ERR_INVALID_ARG, "%s: a reconstruct-8 copy is validated on the host; prepare it outside stream capture",
+                    what);
+    double err = 0.0;
+    cudaError_t e = gauge_recon8_error(dst, prec, aos, src, sprec, srecon, g, s, &err);
+    if (e != cudaSuccess) return check_cuda(e, what);
+    const double tol = recon8_tolerance(prec);
+    if (!(err <= tol))
+        return fail(QCD_ERR_INVALID_ARG,
+                    "%s: reconstruct-8 in %s misses these links by %.3g (limit %.3g): the pivoted 8-real form needs "
+                    "links near the identity; use reconstruct-12",
+                    what, prec_name(prec), err, tol);
+    return QCD_OK;
+}
 
 // ----------------------------------------------------------------- views
 
@@ -211,6 +254,13 @@ GaugeView gauge_view(const qcd_gauge *g, int prec, int recon, cudaStream_t s, qc
         cudaFree(p);
         *st = check_cuda(e, "gauge copy");
         return GaugeView{nullptr, stride};
+    }
+    if (recon == 8) {
+        *st = check_recon8(dst, prec, nullptr, src, g->prec, g->recon, g->lat->geom, s, "gauge copy");
+        if (*st != QCD_OK) {
+            cudaFree(p);
+            return GaugeView{nullptr, stride};
+        }
     }
     gm->derived[key] = {p, bytes};
     return dst;
@@ -627,11 +677,16 @@ qcd_status qcd_gauge_upload(qcd_gauge *g, const double *host, void *stream)
     cudaError_t e = cudaMallocAsync(&stage, bytes, s);
     if (e != cudaSuccess) return check_cuda(e, "gauge_upload: staging");
     e = cudaMemcpyAsync(stage, host, bytes, cudaMemcpyHostToDevice, s);
+    const GaugeView dst{g->data, g->lat->stride};
     if (e == cudaSuccess)
-        e = launch_gauge_pack(GaugeView{g->data, g->lat->stride}, g->prec, g->recon, static_cast<const double2 *>(stage),
-                              g->lat->geom, s);
+        e = launch_gauge_pack(dst, g->prec, g->recon, static_cast<const double2 *>(stage), g->lat->geom, s);
+    qcd_status st = QCD_OK;
+    if (e == cudaSuccess && g->recon == 8)
+        st = check_recon8(dst, g->prec, static_cast<const double2 *>(stage), dst, g->prec, g->recon, g->lat->geom, s,
+                          "gauge_upload");
     cudaError_t e2 = cudaFreeAsync(stage, s);
     if (e == cudaSuccess) e = e2;
+    if (st != QCD_OK) return st;
     return check_cuda(e, "gauge_upload");
 }
 

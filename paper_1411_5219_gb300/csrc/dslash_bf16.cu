@@ -7,6 +7,7 @@ cudaError_t launch_dslash_bf16(int recon, const DslashLaunch &a, cudaStream_t s)
 {
     if (recon == 18) return launch_dslash_fmt<SpBF16, G16<__nv_bfloat16, 18>>(a, s);
     if (recon == 12) return launch_dslash_fmt<SpBF16, G16<__nv_bfloat16, 12>>(a, s);
+    if (recon == 8) return launch_dslash_fmt<SpBF16, G16<__nv_bfloat16, 8>>(a, s);
     return cudaErrorInvalidValue;
 }
 

@@ -172,15 +172,16 @@ __host__ __device__ constexpr int dslash_min_blocks()
 
 // Minimum resident blocks for __launch_bounds__: the FP64-family kernels at
 // 64 threads need six (<= 170 registers); the 4-byte kernels are not capped
-// (64- and 85-register caps spill and measured slower at 24^3x8 and 48^3x12).
-template <typename SF, int TPB>
+// (64- and 85-register caps spill and measured slower at 24^3x8 and 48^3x12),
+// nor is FP64 reconstruct-8, whose rebuild would spill under the cap.
+template <typename SF, typename GF, int TPB>
 __host__ __device__ constexpr int dslash_min_blocks_tpb()
 {
-    return sizeof(typename SF::R) == 8 ? (TPB == 64 ? 6 : 1) : 1;
+    return sizeof(typename SF::R) == 8 && GF::kRecon_ != 8 ? (TPB == 64 ? 6 : 1) : 1;
 }
 
 template <typename SF, typename GF, int kDagger, int kEpi, bool kReduce, int TPB>
-__global__ void __launch_bounds__(TPB, (dslash_min_blocks_tpb<SF, TPB>())) dslash_kernel(const DslashLaunch a)
+__global__ void __launch_bounds__(TPB, (dslash_min_blocks_tpb<SF, GF, TPB>())) dslash_kernel(const DslashLaunch a)
 {
     using R = typename SF::R;
     if (a.check_status && a.state->status != CG_RUNNING) return;

@@ -3,6 +3,8 @@
 // in the storage precision; CL2QCD arXiv:1411.5219 Sec. 4 keeps device
 // buffers in SoA form because GPUs need it for coalesced access), plus the
 // conversion of a gauge field between device formats.
+#include <cstring>
+
 #include "qcd_ops.h"
 
 namespace qcd {
@@ -48,7 +50,7 @@ __global__ void gauge_pack_kernel(const GaugeView dst, const double2 *aos, const
         const double2 *src = aos + ((size_t)lex * 4 + mu) * 9;
 #pragma unroll
         for (int k = 0; k < 9; ++k) u.m[k / 3][k % 3] = mk(src[k].x, src[k].y);
-        GF::store(dst, c.parity * 4 + mu, c.half, cvt_link<typename GF::R>(u));
+        GF::store64(dst, c.parity * 4 + mu, c.half, u);
     }
 }
 
@@ -58,7 +60,59 @@ __global__ void gauge_convert_kernel(const GaugeView dst, const GaugeView src, c
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int b = blockIdx.y;
     if (i >= h) return;
-    GO::store(dst, b, i, cvt_link<typename GO::R>(GI::load(src, b, i)));
+    GO::store64(dst, b, i, cvt_link<double>(GI::load(src, b, i)));
+}
+
+// Largest |entry error| of the links stored in format GF against the FP64
+// reference, over the grid (atomicMax on the bit pattern, which orders
+// non-negative doubles; a non-finite error counts as 1e300).
+template <typename R>
+__device__ __forceinline__ double link_max_err(const Link<R> &v, const Link<double> &u)
+{
+    double m = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            double e = fmax(fabs((double)v.m[a][b].re - u.m[a][b].re), fabs((double)v.m[a][b].im - u.m[a][b].im));
+            if (!(e < 1e300)) e = 1e300;
+            m = fmax(m, e);
+        }
+    return m;
+}
+__device__ __forceinline__ void max_into(unsigned long long *out, double e)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) e = fmax(e, __shfl_xor_sync(0xffffffffu, e, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(e));
+}
+
+template <typename GF>
+__global__ void gauge_check_aos_kernel(const GaugeView dst, const double2 *aos, const Geom g, unsigned long long *out)
+{
+    const int lex = blockIdx.x * blockDim.x + threadIdx.x;
+    double e = 0.0;
+    if (lex < 2 * g.h) {
+        const LexCoords c = lex_coords(g, lex);
+        for (int mu = 0; mu < 4; ++mu) {
+            Link<double> u;
+            const double2 *src = aos + ((size_t)lex * 4 + mu) * 9;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) u.m[k / 3][k % 3] = mk(src[k].x, src[k].y);
+            e = fmax(e, link_max_err(GF::load(dst, c.parity * 4 + mu, c.half), u));
+        }
+    }
+    max_into(out, e);
+}
+
+template <typename GO, typename GI>
+__global__ void gauge_check_kernel(const GaugeView dst, const GaugeView src, const int h, unsigned long long *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.y;
+    double e = 0.0;
+    if (i < h) e = link_max_err(GO::load(dst, b, i), cvt_link<double>(GI::load(src, b, i)));
+    max_into(out, e);
 }
 
 template <typename SF>
@@ -135,6 +189,18 @@ __global__ void spinor_unpack_kernel(double2 *aos, const FieldView src, const in
     } else if (prec == QCD_PREC_BF16 && recon == 12) {                        \
         using GF = G16<__nv_bfloat16, 12>;                                    \
         __VA_ARGS__;                                                          \
+    } else if (prec == QCD_PREC_F64 && recon == 8) {                          \
+        using GF = GF64<8>;                                                   \
+        __VA_ARGS__;                                                          \
+    } else if (prec == QCD_PREC_F32 && recon == 8) {                          \
+        using GF = GF32<8>;                                                   \
+        __VA_ARGS__;                                                          \
+    } else if (prec == QCD_PREC_F16 && recon == 8) {                          \
+        using GF = G16<__half, 8>;                                            \
+        __VA_ARGS__;                                                          \
+    } else if (prec == QCD_PREC_BF16 && recon == 8) {                         \
+        using GF = G16<__nv_bfloat16, 8>;                                     \
+        __VA_ARGS__;                                                          \
     } else if (prec == QCD_PREC_DF64 && recon == 18) {                        \
         using GF = GDF64<18>;                                                 \
         __VA_ARGS__;                                                          \
@@ -188,6 +254,40 @@ cudaError_t launch_gauge_convert(const GaugeView &dst, int dprec, int drecon, co
                 QCD_G_CASES(sprec, srecon, GI, gauge_convert_kernel<GO, GI><<<grid, 128, 0, s>>>(dst, src, g.h)));
     note_launches();
     return cudaGetLastError();
+}
+
+// Largest entry error of a reconstruct-8 field `dst` against its FP64
+// source: the host array staged at `aos` (when not null) or the device
+// field `src` in format (sprec, srecon).  Synchronises the stream.
+cudaError_t gauge_recon8_error(const GaugeView &dst, int prec, const double2 *aos, const GaugeView &src, int sprec,
+                               int srecon, const Geom &g, cudaStream_t s, double *max_err)
+{
+    unsigned long long *d = nullptr, hbits = 0;
+    cudaError_t e = cudaMallocAsync(&d, sizeof(*d), s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(d, 0, sizeof(*d), s);
+    if (e == cudaSuccess) {
+        e = [&]() -> cudaError_t {
+            if (aos) {
+                QCD_G_CASES(prec, 8, GF, gauge_check_aos_kernel<GF><<<(2 * g.h + 127) / 128, 128, 0, s>>>(dst, aos, g, d));
+            } else {
+                const dim3 grid((g.h + 127) / 128, 8);
+                QCD_G_CASES(prec, 8, GO,
+                            QCD_G_CASES(sprec, srecon, GI, gauge_check_kernel<GO, GI><<<grid, 128, 0, s>>>(dst, src, g.h, d)));
+            }
+            return cudaSuccess;
+        }();
+        note_launches();
+        if (e == cudaSuccess) e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hbits, d, sizeof(hbits), cudaMemcpyDeviceToHost, s);
+    cudaError_t e2 = cudaFreeAsync(d, s);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    double v;
+    memcpy(&v, &hbits, sizeof(v));
+    *max_err = v;
+    return e;
 }
 
 cudaError_t launch_spinor_pack(const FieldView &dst, int parity, const double2 *aos, const Geom &g, cudaStream_t s)

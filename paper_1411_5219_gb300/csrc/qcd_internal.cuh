@@ -20,6 +20,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "../../include/qcd.h"
 #include "df64.cuh"
 
@@ -352,8 +354,83 @@ struct Sp16 {
 using SpF16 = Sp16<__half, true>;
 using SpBF16 = Sp16<__nv_bfloat16, false>;
 
-// Gauge storage formats: kRecon = 18 (full matrix) or 12 (rows 0 and 1;
-// row 2 = conj(row0 x row1), valid for SU(3)).
+// Gauge storage formats: kRecon = 18 (full matrix), 12 (rows 0 and 1;
+// row 2 = conj(row0 x row1), valid for SU(3)) or 8 (eight reals, below).
+//
+// Reconstruct-8, pivoted for links near the identity.  Work on W = U with
+// its columns reversed (W_ij = U_i,2-j; unitary with det W = -1), so that
+// the two entries recovered from a norm, w02 = U_00 and w20 = U_22, are the
+// large diagonal ones and the divisor N = |w01|^2 + |w02|^2 is close to 1.
+// Stored: w00, w01, w10 (complex) and the half-angle tangents t = tan(arg/2)
+// of w02 and w20 (a phase e^{i arg} = ((1 - t^2) + 2 i t) / (1 + t^2), one
+// division instead of sin and cos; the angular error stays below the storage
+// rounding of t).  Rows a, b, c of W: |w02| and |w20| follow from the unit
+// norm of row a and column 0; orthogonality of a and b together with
+// c = -conj(a x b) (det W = -1) gives a 2x2 linear system for w11, w12 with
+// determinant -N; the rest of row c is -conj(a x b).
+template <typename R>
+__host__ __device__ __forceinline__ R half_angle_tan(cx<R> w, R tmax)
+{
+    const R a = sqrt(w.re * w.re + w.im * w.im);
+    if (!(a > R(0))) return R(0);
+    R t;
+    if (w.re >= R(0))
+        t = w.im / (a + w.re);
+    else
+        t = w.im == R(0) ? tmax : (a - w.re) / w.im;
+    return t > tmax ? tmax : (t < -tmax ? -tmax : t);
+}
+
+template <typename R>
+__host__ __device__ __forceinline__ void recon8_encode(const Link<R> &u, R p[8], R tmax)
+{
+    // W = U with reversed columns
+    const cx<R> w00 = u.m[0][2], w01 = u.m[0][1], w02 = u.m[0][0], w10 = u.m[1][2], w20 = u.m[2][2];
+    p[0] = w00.re;
+    p[1] = w00.im;
+    p[2] = w01.re;
+    p[3] = w01.im;
+    p[4] = w10.re;
+    p[5] = w10.im;
+    p[6] = half_angle_tan(w02, tmax);
+    p[7] = half_angle_tan(w20, tmax);
+}
+
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> unit_phase(R t)
+{
+    const R r = R(1) / (R(1) + t * t);
+    return {(R(1) - t * t) * r, R(2) * t * r};
+}
+
+template <typename R>
+__device__ __forceinline__ Link<R> recon8_decode(const R p[8])
+{
+    const cx<R> w00 = mk(p[0], p[1]), w01 = mk(p[2], p[3]), w10 = mk(p[4], p[5]);
+    const R n00 = w00.re * w00.re + w00.im * w00.im;
+    const R n01 = w01.re * w01.re + w01.im * w01.im;
+    const R n10 = w10.re * w10.re + w10.im * w10.im;
+    const R r02 = R(1) - n00 - n01, r20 = R(1) - n00 - n10;
+    const R a02 = sqrt(r02 > R(0) ? r02 : R(0)), a20 = sqrt(r20 > R(0) ? r20 : R(0));
+    const cx<R> w02 = a02 * unit_phase(p[6]), w20 = a20 * unit_phase(p[7]);
+    const R inv_n = R(1) / (n01 + a02 * a02);
+    const cx<R> w11 = inv_n * (cmul(conjg(w20), conjg(w02)) - cmul(cmul(w01, conjg(w00)), w10));
+    const cx<R> w12 = -(inv_n * (cmul(cmul(w02, conjg(w00)), w10) + cmul(conjg(w01), conjg(w20))));
+    const cx<R> w21 = -conjg(cmul(w02, w10) - cmul(w00, w12));
+    const cx<R> w22 = -conjg(cmul(w00, w11) - cmul(w01, w10));
+    Link<R> u;  // undo the column reversal
+    u.m[0][0] = w02;
+    u.m[0][1] = w01;
+    u.m[0][2] = w00;
+    u.m[1][0] = w12;
+    u.m[1][1] = w11;
+    u.m[1][2] = w10;
+    u.m[2][0] = w22;
+    u.m[2][1] = w21;
+    u.m[2][2] = w20;
+    return u;
+}
+
 template <int kRecon, typename R>
 __device__ __forceinline__ void reconstruct_row2(Link<R> &u)
 {
@@ -368,8 +445,9 @@ template <int kRecon>
 struct GF64 {
     using R = double;
     static constexpr int kRecon_ = kRecon;
-    static constexpr int kPlanes = kRecon / 2;  // double2 (one complex) per plane
+    static constexpr int kPlanes = kRecon / 2;  // double2 (one complex, or two reals of recon-8) per plane
     static constexpr size_t kBytesPerLink = kRecon * 8;
+    static constexpr double kTmax = 1e150;      // recon-8 clamp of tan(arg/2)
     struct Raw {
         double2 d[kPlanes];
     };
@@ -383,29 +461,35 @@ struct GF64 {
     }
     __device__ __forceinline__ static Link<R> decode(const Raw &r)
     {
-        Link<R> u;
+        if constexpr (kRecon == 8) {
+            const double p[8] = {r.d[0].x, r.d[0].y, r.d[1].x, r.d[1].y, r.d[2].x, r.d[2].y, r.d[3].x, r.d[3].y};
+            return recon8_decode<double>(p);
+        } else {
+            Link<R> u;
 #pragma unroll
-        for (int k = 0; k < kPlanes; ++k) u.m[k / 3][k % 3] = mk(r.d[k].x, r.d[k].y);
-        reconstruct_row2<kRecon>(u);
-        return u;
-    }
-    __device__ __forceinline__ static Link<R> load(const GaugeView &g, int block, int i)
-    {
-        Link<R> u;
-        const double2 *p = static_cast<const double2 *>(g.data) + (size_t)block * kPlanes * g.stride + i;
-#pragma unroll
-        for (int k = 0; k < kPlanes; ++k) {
-            double2 d = __ldg(p + (size_t)k * g.stride);
-            u.m[k / 3][k % 3] = mk(d.x, d.y);
+            for (int k = 0; k < kPlanes; ++k) u.m[k / 3][k % 3] = mk(r.d[k].x, r.d[k].y);
+            reconstruct_row2<kRecon>(u);
+            return u;
         }
-        reconstruct_row2<kRecon>(u);
-        return u;
     }
+    __device__ __forceinline__ static Link<R> load(const GaugeView &g, int block, int i) { return decode(fetch(g, block, i)); }
     __device__ __forceinline__ static void store(const GaugeView &g, int block, int i, const Link<R> &u)
     {
         double2 *p = static_cast<double2 *>(g.data) + (size_t)block * kPlanes * g.stride + i;
+        if constexpr (kRecon == 8) {
+            double q[8];
+            recon8_encode<double>(u, q, kTmax);
 #pragma unroll
-        for (int k = 0; k < kPlanes; ++k) p[(size_t)k * g.stride] = make_double2(u.m[k / 3][k % 3].re, u.m[k / 3][k % 3].im);
+            for (int k = 0; k < 4; ++k) p[(size_t)k * g.stride] = make_double2(q[2 * k], q[2 * k + 1]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < kPlanes; ++k)
+                p[(size_t)k * g.stride] = make_double2(u.m[k / 3][k % 3].re, u.m[k / 3][k % 3].im);
+        }
+    }
+    __device__ __forceinline__ static void store64(const GaugeView &g, int block, int i, const Link<double> &u)
+    {
+        store(g, block, i, u);
     }
 };
 
@@ -413,10 +497,11 @@ template <int kRecon>
 struct GF32 {
     using R = float;
     static constexpr int kRecon_ = kRecon;
-    // recon-18: nine float2 planes; recon-12: three float4 planes
-    static constexpr int kPlanes = kRecon == 18 ? 9 : 3;
+    // recon-18: nine float2 planes; recon-12: three float4 planes; recon-8: two float4 planes
+    static constexpr int kPlanes = kRecon == 18 ? 9 : kRecon == 12 ? 3 : 2;
     static constexpr size_t kBytesPerLink = kRecon * 4;
-    // recon-18: nine float2; recon-12: three float4 (kept as six float2)
+    static constexpr float kTmax = 1e18f;  // recon-8 clamp of tan(arg/2) (t^2 stays finite)
+    // recon-18: nine float2; recon-12 / recon-8: float4 planes kept as float2 pairs
     struct Raw {
         float2 d[kRecon / 2];
     };
@@ -430,7 +515,7 @@ struct GF32 {
         } else {
             const float4 *p = static_cast<const float4 *>(g.data) + (size_t)block * kPlanes * g.stride + i;
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
+            for (int k = 0; k < kPlanes; ++k) {
                 const float4 d = __ldg(p + (size_t)k * g.stride);
                 r.d[2 * k] = make_float2(d.x, d.y);
                 r.d[2 * k + 1] = make_float2(d.z, d.w);
@@ -440,47 +525,55 @@ struct GF32 {
     }
     __device__ __forceinline__ static Link<R> decode(const Raw &r)
     {
-        Link<R> u;
-#pragma unroll
-        for (int k = 0; k < kRecon / 2; ++k) u.m[k / 3][k % 3] = mk(r.d[k].x, r.d[k].y);
-        reconstruct_row2<kRecon>(u);
-        return u;
-    }
-    __device__ __forceinline__ static Link<R> load(const GaugeView &g, int block, int i)
-    {
-        Link<R> u;
-        if (kRecon == 18) {
-            const float2 *p = static_cast<const float2 *>(g.data) + (size_t)block * kPlanes * g.stride + i;
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                float2 d = __ldg(p + (size_t)k * g.stride);
-                u.m[k / 3][k % 3] = mk(d.x, d.y);
-            }
+        if constexpr (kRecon == 8) {
+            const float p[8] = {r.d[0].x, r.d[0].y, r.d[1].x, r.d[1].y, r.d[2].x, r.d[2].y, r.d[3].x, r.d[3].y};
+            return recon8_decode<float>(p);
         } else {
-            const float4 *p = static_cast<const float4 *>(g.data) + (size_t)block * kPlanes * g.stride + i;
+            Link<R> u;
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                float4 d = __ldg(p + (size_t)k * g.stride);
-                u.m[(2 * k) / 3][(2 * k) % 3] = mk(d.x, d.y);
-                u.m[(2 * k + 1) / 3][(2 * k + 1) % 3] = mk(d.z, d.w);
-            }
-            reconstruct_row2<12>(u);
+            for (int k = 0; k < kRecon / 2; ++k) u.m[k / 3][k % 3] = mk(r.d[k].x, r.d[k].y);
+            reconstruct_row2<kRecon>(u);
+            return u;
         }
-        return u;
     }
+    __device__ __forceinline__ static Link<R> load(const GaugeView &g, int block, int i) { return decode(fetch(g, block, i)); }
     __device__ __forceinline__ static void store(const GaugeView &g, int block, int i, const Link<R> &u)
     {
         if (kRecon == 18) {
             float2 *p = static_cast<float2 *>(g.data) + (size_t)block * kPlanes * g.stride + i;
 #pragma unroll
             for (int k = 0; k < 9; ++k) p[(size_t)k * g.stride] = make_float2(u.m[k / 3][k % 3].re, u.m[k / 3][k % 3].im);
-        } else {
+        } else if (kRecon == 12) {
             float4 *p = static_cast<float4 *>(g.data) + (size_t)block * kPlanes * g.stride + i;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 const cx<R> a = u.m[(2 * k) / 3][(2 * k) % 3], b = u.m[(2 * k + 1) / 3][(2 * k + 1) % 3];
                 p[(size_t)k * g.stride] = make_float4(a.re, a.im, b.re, b.im);
             }
+        } else {
+            float4 *p = static_cast<float4 *>(g.data) + (size_t)block * kPlanes * g.stride + i;
+            float q[8];
+            recon8_encode<float>(u, q, kTmax);
+            p[0] = make_float4(q[0], q[1], q[2], q[3]);
+            p[(size_t)g.stride] = make_float4(q[4], q[5], q[6], q[7]);
+        }
+    }
+    // FP64 source: the recon-8 parameters are computed in FP64 and rounded once
+    __device__ __forceinline__ static void store64(const GaugeView &g, int block, int i, const Link<double> &u)
+    {
+        if constexpr (kRecon == 8) {
+            double q[8];
+            recon8_encode<double>(u, q, (double)kTmax);
+            float4 *p = static_cast<float4 *>(g.data) + (size_t)block * kPlanes * g.stride + i;
+            p[0] = make_float4((float)q[0], (float)q[1], (float)q[2], (float)q[3]);
+            p[(size_t)g.stride] = make_float4((float)q[4], (float)q[5], (float)q[6], (float)q[7]);
+        } else {
+            Link<R> v;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) v.m[a][b] = mk((float)u.m[a][b].re, (float)u.m[a][b].im);
+            store(g, block, i, v);
         }
     }
 };
@@ -522,6 +615,15 @@ struct GDF64 {
             p[(size_t)k * g.stride] = make_float4(a.re.hi, a.im.hi, a.re.lo, a.im.lo);
         }
     }
+    __device__ __forceinline__ static void store64(const GaugeView &g, int block, int i, const Link<double> &u)
+    {
+        Link<R> v;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) v.m[a][b] = cx<R>{df(u.m[a][b].re), df(u.m[a][b].im)};
+        store(g, block, i, v);
+    }
 };
 
 // 16-bit links (FP16 or BF16), unscaled (|U_ab| <= 1).  recon-18: nine
@@ -530,9 +632,11 @@ template <typename H, int kRecon>
 struct G16 {
     using R = float;
     static constexpr int kRecon_ = kRecon;
-    static constexpr int kPlanes = kRecon == 18 ? 9 : 3;
+    static constexpr int kPlanes = kRecon == 18 ? 9 : kRecon == 12 ? 3 : 1;
     static constexpr size_t kBytesPerLink = kRecon * 2;
-    // one 32-bit word (two 16-bit reals) per complex entry
+    // recon-8 clamp of tan(arg/2): inside the FP16 range (BF16 has the FP32 range)
+    static constexpr double kTmax = std::is_same<H, __half>::value ? 32768.0 : 1e18;
+    // one 32-bit word (two 16-bit reals) per complex entry / recon-8 pair
     struct Raw {
         uint32_t w[kRecon / 2];
     };
@@ -543,7 +647,7 @@ struct G16 {
             const uint32_t *p = static_cast<const uint32_t *>(g.data) + (size_t)block * kPlanes * g.stride + i;
 #pragma unroll
             for (int k = 0; k < 9; ++k) r.w[k] = __ldg(p + (size_t)k * g.stride);
-        } else {
+        } else if (kRecon == 12) {
             const uint2 *p = static_cast<const uint2 *>(g.data) + (size_t)block * kPlanes * g.stride + i;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
@@ -551,42 +655,43 @@ struct G16 {
                 r.w[2 * k] = w.x;
                 r.w[2 * k + 1] = w.y;
             }
+        } else {
+            const uint4 w = __ldg(static_cast<const uint4 *>(g.data) + (size_t)block * g.stride + i);
+            r.w[0] = w.x;
+            r.w[1] = w.y;
+            r.w[2] = w.z;
+            r.w[3] = w.w;
         }
         return r;
     }
     __device__ __forceinline__ static Link<R> decode(const Raw &r)
     {
-        Link<R> u;
+        if constexpr (kRecon == 8) {
+            float p[8];
 #pragma unroll
-        for (int k = 0; k < kRecon / 2; ++k) {
-            const float2 f = Half16<H>::to2(r.w[k]);
-            u.m[k / 3][k % 3] = mk(f.x, f.y);
-        }
-        reconstruct_row2<kRecon>(u);
-        return u;
-    }
-    __device__ __forceinline__ static Link<R> load(const GaugeView &g, int block, int i)
-    {
-        Link<R> u;
-        if (kRecon == 18) {
-            const uint32_t *p = static_cast<const uint32_t *>(g.data) + (size_t)block * kPlanes * g.stride + i;
+            for (int k = 0; k < 4; ++k) {
+                const float2 f = Half16<H>::to2(r.w[k]);
+                p[2 * k] = f.x;
+                p[2 * k + 1] = f.y;
+            }
+            return recon8_decode<float>(p);
+        } else {
+            Link<R> u;
 #pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                float2 f = Half16<H>::to2(__ldg(p + (size_t)k * g.stride));
+            for (int k = 0; k < kRecon / 2; ++k) {
+                const float2 f = Half16<H>::to2(r.w[k]);
                 u.m[k / 3][k % 3] = mk(f.x, f.y);
             }
-        } else {
-            const uint2 *p = static_cast<const uint2 *>(g.data) + (size_t)block * kPlanes * g.stride + i;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                uint2 w = __ldg(p + (size_t)k * g.stride);
-                float2 a = Half16<H>::to2(w.x), b = Half16<H>::to2(w.y);
-                u.m[(2 * k) / 3][(2 * k) % 3] = mk(a.x, a.y);
-                u.m[(2 * k + 1) / 3][(2 * k + 1) % 3] = mk(b.x, b.y);
-            }
-            reconstruct_row2<12>(u);
+            reconstruct_row2<kRecon>(u);
+            return u;
         }
-        return u;
+    }
+    __device__ __forceinline__ static Link<R> load(const GaugeView &g, int block, int i) { return decode(fetch(g, block, i)); }
+    __device__ __forceinline__ static void store_params(const GaugeView &g, int block, int i, const float q[8])
+    {
+        uint4 *p = static_cast<uint4 *>(g.data) + (size_t)block * g.stride + i;
+        *p = make_uint4(Half16<H>::from2(q[0], q[1]), Half16<H>::from2(q[2], q[3]), Half16<H>::from2(q[4], q[5]),
+                        Half16<H>::from2(q[6], q[7]));
     }
     __device__ __forceinline__ static void store(const GaugeView &g, int block, int i, const Link<R> &u)
     {
@@ -594,13 +699,36 @@ struct G16 {
             uint32_t *p = static_cast<uint32_t *>(g.data) + (size_t)block * kPlanes * g.stride + i;
 #pragma unroll
             for (int k = 0; k < 9; ++k) p[(size_t)k * g.stride] = Half16<H>::from2(u.m[k / 3][k % 3].re, u.m[k / 3][k % 3].im);
-        } else {
+        } else if (kRecon == 12) {
             uint2 *p = static_cast<uint2 *>(g.data) + (size_t)block * kPlanes * g.stride + i;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 const cx<R> a = u.m[(2 * k) / 3][(2 * k) % 3], b = u.m[(2 * k + 1) / 3][(2 * k + 1) % 3];
                 p[(size_t)k * g.stride] = make_uint2(Half16<H>::from2(a.re, a.im), Half16<H>::from2(b.re, b.im));
             }
+        } else {
+            float q[8];
+            recon8_encode<float>(u, q, (float)kTmax);
+            store_params(g, block, i, q);
+        }
+    }
+    // FP64 source: the recon-8 parameters are computed in FP64 and rounded once to FP32, then to 16 bits
+    __device__ __forceinline__ static void store64(const GaugeView &g, int block, int i, const Link<double> &u)
+    {
+        if constexpr (kRecon == 8) {
+            double q[8];
+            recon8_encode<double>(u, q, kTmax);
+            float f[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) f[k] = (float)q[k];
+            store_params(g, block, i, f);
+        } else {
+            Link<R> v;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) v.m[a][b] = mk((float)u.m[a][b].re, (float)u.m[a][b].im);
+            store(g, block, i, v);
         }
     }
 };

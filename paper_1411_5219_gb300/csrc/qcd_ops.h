@@ -82,6 +82,8 @@ cudaError_t launch_gauge_pack(const GaugeView &dst, int prec, int recon, const d
                               cudaStream_t s);
 cudaError_t launch_gauge_convert(const GaugeView &dst, int dprec, int drecon, const GaugeView &src, int sprec,
                                  int srecon, const Geom &g, cudaStream_t s);
+cudaError_t gauge_recon8_error(const GaugeView &dst, int prec, const double2 *aos, const GaugeView &src, int sprec,
+                               int srecon, const Geom &g, cudaStream_t s, double *max_err);
 // parity: 0/1 for a half field in parity-compacted host layout, 2 for a
 // full field in lexicographic host layout.
 cudaError_t launch_spinor_pack(const FieldView &dst, int parity, const double2 *aos, const Geom &g, cudaStream_t s);

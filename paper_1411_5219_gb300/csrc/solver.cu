@@ -408,7 +408,7 @@ qcd_status qcd::solve_impl(const qcd_gauge *g, qcd_spinor *const *x, const qcd_s
     if (prm->inner_prec < QCD_PREC_F64 || prm->inner_prec > QCD_PREC_DF64)
         return fail(QCD_ERR_INVALID_ARG, "solve_cg: bad inner_prec");
     const bool mixed = prm->inner_prec != QCD_PREC_F64;
-    if (mixed && prm->inner_recon != 18 && prm->inner_recon != 12)
+    if (mixed && prm->inner_recon != 18 && prm->inner_recon != 12 && prm->inner_recon != 8)
         return fail(QCD_ERR_INVALID_ARG, "solve_cg: bad inner_recon");
     if (mixed && !(prm->reliable_delta > 0.0 && prm->reliable_delta < 1.0))
         return fail(QCD_ERR_INVALID_ARG, "solve_cg: reliable_delta must be in (0, 1)");

@@ -205,6 +205,8 @@ using GH18 = G16<__half, 18>;
 using GH12 = G16<__half, 12>;
 using GB18 = G16<__nv_bfloat16, 18>;
 using GB12 = G16<__nv_bfloat16, 12>;
+using GH8 = G16<__half, 8>;
+using GB8 = G16<__nv_bfloat16, 8>;
 
 }  // namespace
 
@@ -233,24 +235,28 @@ using GB12 = G16<__nv_bfloat16, 12>;
 cudaError_t launch_dslash_ks(int prec, int recon, const KsLaunch &a, cudaStream_t s)
 {
     const dim3 grid((a.g.h + 127) / 128 * (a.both ? 2 : 1)), block(128);
-    if (recon != 18 && recon != 12) return cudaErrorInvalidValue;
-    const bool r18 = recon == 18;
+    if (recon != 18 && recon != 12 && recon != 8) return cudaErrorInvalidValue;
+    const int r = recon;
     switch (prec) {
     case QCD_PREC_F64:
-        if (r18) dslash_ks_kernel<KS64, GF64<18>><<<grid, block, 0, s>>>(a);
-        else dslash_ks_kernel<KS64, GF64<12>><<<grid, block, 0, s>>>(a);
+        if (r == 18) dslash_ks_kernel<KS64, GF64<18>><<<grid, block, 0, s>>>(a);
+        else if (r == 12) dslash_ks_kernel<KS64, GF64<12>><<<grid, block, 0, s>>>(a);
+        else dslash_ks_kernel<KS64, GF64<8>><<<grid, block, 0, s>>>(a);
         break;
     case QCD_PREC_F32:
-        if (r18) dslash_ks_kernel<KS32, GF32<18>><<<grid, block, 0, s>>>(a);
-        else dslash_ks_kernel<KS32, GF32<12>><<<grid, block, 0, s>>>(a);
+        if (r == 18) dslash_ks_kernel<KS32, GF32<18>><<<grid, block, 0, s>>>(a);
+        else if (r == 12) dslash_ks_kernel<KS32, GF32<12>><<<grid, block, 0, s>>>(a);
+        else dslash_ks_kernel<KS32, GF32<8>><<<grid, block, 0, s>>>(a);
         break;
     case QCD_PREC_F16:
-        if (r18) dslash_ks_kernel<KS16<__half, true>, GH18><<<grid, block, 0, s>>>(a);
-        else dslash_ks_kernel<KS16<__half, true>, GH12><<<grid, block, 0, s>>>(a);
+        if (r == 18) dslash_ks_kernel<KS16<__half, true>, GH18><<<grid, block, 0, s>>>(a);
+        else if (r == 12) dslash_ks_kernel<KS16<__half, true>, GH12><<<grid, block, 0, s>>>(a);
+        else dslash_ks_kernel<KS16<__half, true>, GH8><<<grid, block, 0, s>>>(a);
         break;
     case QCD_PREC_BF16:
-        if (r18) dslash_ks_kernel<KS16<__nv_bfloat16, false>, GB18><<<grid, block, 0, s>>>(a);
-        else dslash_ks_kernel<KS16<__nv_bfloat16, false>, GB12><<<grid, block, 0, s>>>(a);
+        if (r == 18) dslash_ks_kernel<KS16<__nv_bfloat16, false>, GB18><<<grid, block, 0, s>>>(a);
+        else if (r == 12) dslash_ks_kernel<KS16<__nv_bfloat16, false>, GB12><<<grid, block, 0, s>>>(a);
+        else dslash_ks_kernel<KS16<__nv_bfloat16, false>, GB8><<<grid, block, 0, s>>>(a);
         break;
     default:
         return cudaErrorInvalidValue;

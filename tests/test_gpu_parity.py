@@ -637,7 +637,8 @@ def ks_half(chi, parity):
 
 
 @pytest.mark.parametrize("dims", DIMS)
-@pytest.mark.parametrize("prec,recon", [("f64", 18), ("f64", 12), ("f32", 12), ("f16", 12), ("bf16", 12)])
+@pytest.mark.parametrize("prec,recon", [("f64", 18), ("f64", 12), ("f32", 12), ("f16", 12), ("bf16", 12),
+                                        ("f64", 8), ("f32", 8), ("f16", 8), ("bf16", 8)])
 def test_dslash_ks_matches_oracle(q, dims, prec, recon):
     lat, U, g = gauge(q, dims, recon=recon)
     lx, ly, lz, lt = dims
@@ -666,3 +667,117 @@ def test_dslash_ks_full_point_source_and_roundtrip(q):
     assert F.rel_err(out, oracle.dks(U, chi)) <= 1e-13
     with pytest.raises(q.QcdError):
         q.apply_dslash(g, so, si)  # Wilson operator on staggered fields
+
+
+# ------------------------------------------------------------ reconstruct-8
+
+@pytest.mark.parametrize("dims", DIMS)
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16"])
+def test_dslash_recon8_matches_oracle(q, dims, prec):
+    """Pivoted 8-real links on near-identity fields: FP64 rebuilds them to
+    the 1e-13 Dslash target, the other formats to their storage tolerance."""
+    lat, U, g = gauge(q, dims, recon=8)
+    psi = syn.gaussian_spinor(dims, 70)
+    for out_parity in (0, 1):
+        half_in = syn.to_half(psi, 1 - out_parity)
+        for dagger in (False, True):
+            want = oracle.dhop_eo(U, half_in, out_parity, dagger=dagger)
+            si = q.Spinor(lat, "odd" if out_parity == 0 else "even", prec)
+            so = q.Spinor(lat, "even" if out_parity == 0 else "odd", prec)
+            si.upload(half_in)
+            q.apply_dslash(g, so, si, dagger=dagger)
+            err = F.rel_err(so.download(), want)
+            assert err <= tol_of(prec), (dims, prec, out_parity, dagger, err)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+def test_recon8_full_and_schur_operators(q, prec):
+    dims = (8, 6, 4, 10)
+    kappa, mu = 0.16, 0.01
+    lat, U, g = gauge(q, dims, recon=8)
+    psi = syn.gaussian_spinor(dims, 71)
+    si, so = q.Spinor(lat, "full", prec), q.Spinor(lat, "full", prec)
+    si.upload(psi)
+    q.apply_M(g, so, si, kappa, mu, eo=False)
+    assert F.rel_err(so.download(), oracle.apply_m(U, psi, kappa, mu)) <= tol_of(prec)
+    xe = syn.to_half(psi, 0)
+    ei, eo_ = q.Spinor(lat, "even", prec), q.Spinor(lat, "even", prec)
+    ei.upload(xe)
+    q.apply_M(g, eo_, ei, kappa, mu, eo=True, dagger=True)
+    assert F.rel_err(eo_.download(), oracle.apply_mhat(U, xe, kappa, mu, dagger=True)) <= tol_of(prec)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+def test_recon8_dslash_multi(q, prec):
+    dims = (6, 4, 2, 8)
+    lat, U, g = gauge(q, dims, recon=8)
+    srcs = sources_12_point_4_gauss(dims, 72)
+    ins, outs = [], []
+    for psi in srcs:
+        si = q.Spinor(lat, "odd", prec)
+        si.upload(syn.to_half(psi, 1))
+        ins.append(si)
+        outs.append(q.Spinor(lat, "even", prec))
+    q.apply_dslash_multi(g, outs, ins, dagger=True)
+    for k, psi in enumerate(srcs):
+        want = oracle.dhop_eo(U, syn.to_half(psi, 1), 0, dagger=True)
+        if np.any(want):
+            assert F.rel_err(outs[k].download(), want) <= tol_of(prec), k
+
+
+@pytest.mark.parametrize("inner", ["f32", "f16", "bf16"])
+def test_solve_inner_recon8(q, inner):
+    """Mixed-precision CG with the inner operator on reconstruct-8 links
+    (from an FP64 reconstruct-18 field) reaches the FP64 target."""
+    dims = (8, 8, 8, 4)
+    kappa, mu = 0.16, 0.01
+    lat, U, g = gauge(q, dims, eps=0.2, seed=77)
+    src = syn.gaussian_spinor(dims, 73)
+    b, x = q.Spinor(lat, "full", "f64"), q.Spinor(lat, "full", "f64")
+    b.upload(src)
+    status, st = q.solve_cg(g, x, b, kappa, mu, tol=1e-10, inner_prec=inner, inner_recon=8)
+    assert status == 0 and st["true_rel_residual"] <= 1e-10
+    xo, _ = oracle.solve_eo(U, src, kappa, mu, tol=1e-12)
+    assert F.rel_err(x.download(), xo) <= 1e-7
+
+
+def test_recon8_refuses_links_far_from_identity(q):
+    """Broad link distributions put the pivot out of its range: the library
+    refuses the field instead of storing a lossy one."""
+    dims = (4, 4, 4, 4)
+    lat = q.Lattice(dims, -1)
+    U = syn.gauge_field(dims, 1.5, 1104)
+    g16 = q.Gauge(lat, "f16", 8)
+    with pytest.raises(q.QcdError) as ei:
+        g16.upload(U)
+    assert ei.value.status == 1 and "reconstruct-8" in str(ei.value)
+    g = q.Gauge(lat, "f64", 18)
+    g.upload(U)
+    for prec in ("f32", "f16", "bf16"):
+        with pytest.raises(q.QcdError):
+            g.prepare(prec, 8)
+    g.prepare("f64", 8)  # FP64 still rebuilds these to ~6e-14, inside its 1e-13 limit
+    g.prepare("f16", 12)  # reconstruct-12 is exact for any SU(3) link
+    # near-identity links of the same lattice are accepted in every format
+    g8 = q.Gauge(lat, "f64", 18)
+    g8.upload(syn.gauge_field(dims, 0.3, 1105))
+    for prec in ("f64", "f32", "f16", "bf16"):
+        g8.prepare(prec, 8)
+    with pytest.raises(q.QcdError):
+        g8.prepare("df64", 8)
+
+
+def test_recon8_profile_counts_eight_reals(q):
+    """The profiled algorithmic bytes of a reconstruct-8 launch count 8 reals per link."""
+    dims = (8, 8, 8, 8)
+    lat, U, g = gauge(q, dims, recon=8, eps=0.2, seed=1106)
+    si, so = q.Spinor(lat, "odd", "f16"), q.Spinor(lat, "even", "f16")
+    si.upload(syn.to_half(syn.gaussian_spinor(dims, 74), 1))
+    q.apply_dslash(g, so, si)
+    q.stream_sync()
+    q.profile_begin()
+    q.apply_dslash(g, so, si)
+    pr = q.profile_end()["f16"]
+    h = lat.volume // 2
+    assert pr["launches"] == 1 and pr["bytes"] == h * (8 * 16 + 2 * 52)
+
