@@ -175,7 +175,8 @@ def timed_steps(torch, fn, k, flush):
     s = torch.cuda.current_stream()
     evs = []
     for _ in range(k):
-        flush_l2(flush)
+        if flush is not None:
+            flush_l2(flush)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(s)
         fn()
@@ -185,9 +186,27 @@ def timed_steps(torch, fn, k, flush):
     return [a.elapsed_time(b) * 1e-3 for a, b in evs]
 
 
+def hot_per_launch(torch, fn, k):
+    """Seconds per launch of k back-to-back launches on warm L2.  A ~1 ms
+    spin kernel ahead of them lets the host queue all k before the first
+    runs, so host launch overhead is not timed."""
+    s = torch.cuda.current_stream()
+    fn()
+    torch.cuda._sleep(2_000_000)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(k):
+        fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) * 1e-3 / k
+
+
 # ------------------------------------------------------------------ extras
 
-def dslash_sweep(qcd, torch, flush, hbm, reps=20):
+def dslash_sweep(qcd, torch, flush, hbm, reps=20, fields=None):
+    """Cold-L2 (flushed) and hot-L2 D_eo timings per volume and format; the
+    host gauge fields are kept in `fields` for the CPU oracle timings."""
     from paper_1411_5219_gb300 import synthetic as syn
     out = {}
     fmts = [("f64", 18, 1536), ("f64", 12, 1152), ("f32", 12, 576), ("f16", 12, 296), ("bf16", 12, 288),
@@ -196,6 +215,8 @@ def dslash_sweep(qcd, torch, flush, hbm, reps=20):
         lat = qcd.Lattice(dims, -1)
         U = syn.gauge_field(dims, 0.2, 1002)
         psi = syn.gaussian_spinor(dims, 5)
+        if fields is not None:
+            fields[dims] = (U, syn.to_half(psi, 1))
         h = lat.volume // 2
         row = {}
         for recon in (18, 12, 8):
@@ -211,10 +232,12 @@ def dslash_sweep(qcd, torch, flush, hbm, reps=20):
                     fn()
                 ts = timed_steps(torch, fn, reps, flush)
                 t = float(np.median(ts))
+                t_hot = hot_per_launch(torch, fn, reps)
                 gbs = h * bps / t / 1e9
                 row[f"{prec}_r{recon}"] = {"us": round(t * 1e6, 2), "GB_s": round(gbs, 1),
                                            "frac_hbm": round(gbs / hbm, 3),
-                                           "TFLOP_s": round(h * 1320 / t / 1e12, 3)}
+                                           "TFLOP_s": round(h * 1320 / t / 1e12, 3),
+                                           "hot_us": round(t_hot * 1e6, 2)}
             del g
         out["x".join(map(str, dims))] = row
         del lat
@@ -426,6 +449,42 @@ def cpu_oracle_sample(target_s=15.0):
             "solves_s": 1.0 / (t_it * iters), "cores": oracle.get_threads(), "sample_s": t_it * n}
 
 
+def cpu_oracle_dslash(fields):
+    """The oracle's D_eo on the host cores, all threads and one thread, per
+    sweep volume (one apply each; the 48^3x12 single-thread apply takes ~1 s)."""
+    import oracle
+    out = {}
+    n_all = oracle.get_threads()
+    for dims, (U, half_in) in fields.items():
+        h = half_in.shape[0]
+        row = {}
+        for n in (n_all, 1):
+            oracle.set_threads(n)
+            t0 = time.time()
+            oracle.dhop_eo(U, half_in, 0)
+            dt = time.time() - t0
+            row[f"ms_{n}core"] = round(dt * 1e3, 2)
+            row[f"GB_s_{n}core"] = round(h * 1536 / dt / 1e9, 2)
+        out["x".join(map(str, dims))] = row
+    oracle.set_threads(n_all)
+    return out
+
+
+def cpu_oracle_cg(name="32^3x8"):
+    """One FP64 oracle CG solve of the 32^3x8 twisted-mass even-odd system
+    (configs' C3) on all host cores, to 1e-10."""
+    import oracle
+    from paper_1411_5219_gb300 import synthetic as syn
+    w = syn.WORKLOADS[name]
+    U = syn.gauge_field(w["dims"], w["eps"], w["seed"])
+    b = syn.gaussian_spinor(w["dims"], w["seed"])
+    t0 = time.time()
+    _, st = oracle.solve_eo(U, b, w["kappa"], w["mu"], tol=TOL)
+    dt = time.time() - t0
+    return {"workload": name, "s": round(dt, 3), "solves_s": round(1.0 / dt, 4), "iterations": int(st[0]),
+            "cores": oracle.get_threads()}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -464,7 +523,8 @@ def run_reference(args):
 
 def dslash_only(args):
     """Launch D_eo `reps` times on one volume (for ncu); PREC may list several
-    formats (f16,bf16); prints the event-timed durations per format."""
+    formats (f16,bf16); with --ks the staggered D_KS instead of Wilson.
+    Prints the event-timed durations per format."""
     import torch
     from paper_1411_5219_gb300 import qcd, synthetic as syn
     dims = tuple(int(v) for v in args.dslash[0].split("x"))
@@ -472,14 +532,21 @@ def dslash_only(args):
     lat = qcd.Lattice(dims, -1)
     g = qcd.Gauge(lat, "f64", recon)
     g.upload(syn.gauge_field(dims, 0.2, 1002, device="cuda"))
-    psi = syn.to_half(syn.gaussian_spinor(dims, 5), 1)
+    if args.ks:
+        lx, ly, lz, lt = dims
+        chi = syn.gaussian_complex(7, syn.STREAM_AUX, (lt, lz, ly, lx, 3))
+        psi = np.ascontiguousarray(chi.reshape(-1, 3)[syn.parity_of_sites(dims).reshape(-1) == 1])
+    else:
+        psi = syn.to_half(syn.gaussian_spinor(dims, 5), 1)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     for prec in precs:
         g.prepare(prec, recon)
-        si, so = qcd.Spinor(lat, "odd", prec), qcd.Spinor(lat, "even", prec)
+        si, so = qcd.Spinor(lat, "odd", prec, ks=args.ks), qcd.Spinor(lat, "even", prec, ks=args.ks)
         si.upload(psi)
-        ts = timed_steps(torch, lambda: qcd.apply_dslash(g, so, si), args.reps, flush)
-        print(json.dumps({"dslash": [args.dslash[0], prec, recon], "us": [round(t * 1e6, 2) for t in ts],
+        fn = (lambda: qcd.apply_dslash_ks(g, so, si)) if args.ks else (lambda: qcd.apply_dslash(g, so, si))
+        ts = timed_steps(torch, fn, args.reps, flush)
+        print(json.dumps({"dslash_ks" if args.ks else "dslash": [args.dslash[0], prec, recon],
+                          "us": [round(t * 1e6, 2) for t in ts],
                           "median_us": round(float(np.median(ts)) * 1e6, 2)}), flush=True)
     return 0
 
@@ -497,6 +564,7 @@ def main():
     ap.add_argument("--dslash", nargs=3, metavar=("DIMS", "PREC", "RECON"),
                     help="only launch the even-odd Dslash (e.g. 48x48x48x12 f16 12), for profilers")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--ks", action="store_true", help="with --dslash: the staggered D_KS")
     ap.add_argument("--serve-requests", type=int, default=2000)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -637,9 +705,11 @@ def main():
         del p4
         line["serving"] = serving_block(qcd, torch, n_requests=args.serve_requests)
         line["dslash_ks_sweep"] = dslash_ks_sweep(qcd, torch, flush, hbm)
-        line["dslash_sweep"] = dslash_sweep(qcd, torch, flush, hbm)
-        line["dslash_sweep_note"] = (f"cold L2 (flushed before each launch); GB/s on compulsory bytes per "
-                                     f"output site; frac of {hbm_kind} HBM {hbm} GB/s")
+        host_fields = {}
+        line["dslash_sweep"] = dslash_sweep(qcd, torch, flush, hbm, fields=host_fields)
+        line["dslash_sweep_note"] = (f"us: cold L2 (flushed before each launch), hot_us: mean of back-to-back "
+                                     f"launches queued behind a spin kernel (warm L2); GB/s on "
+                                     f"compulsory bytes per output site (cold); frac of {hbm_kind} HBM {hbm} GB/s")
         try:
             cb = cpu_oracle_sample()
             line["cpu_baseline"] = {"value": cb["solves_s"], "unit": "solves/s", "cores": cb["cores"],
@@ -647,6 +717,8 @@ def main():
                                     "sample": f"{cb['iters_sampled']} FP64 oracle CG iterations of the 24^3x8 "
                                               f"even-odd system ({cb['sample_s']:.1f} s), scaled by the oracle's "
                                               f"{cb['iters_per_solve']} iterations per solve"}
+            line["cpu_baseline"]["dslash"] = cpu_oracle_dslash(host_fields)
+            line["cpu_baseline"]["cg_32x8_twisted"] = cpu_oracle_cg()
         except Exception as e:  # the oracle is a baseline, not the product
             line["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
                                     "sample": f"not run: {e}"}

@@ -309,10 +309,7 @@ def test_dslash_full_size_sampled(q, name):
     checked at 4096 sampled even sites against the oracle, site by site."""
     w = syn.WORKLOADS[name]
     dims = w["dims"]
-    lat = q.Lattice(dims, -1)
-    U = syn.gauge_field(dims, w["eps"], w["seed"])
-    g = q.Gauge(lat, "f64", 18)
-    g.upload(U)
+    lat, U, g = gauge(q, dims, eps=w["eps"], seed=w["seed"])
     psi = syn.gaussian_spinor(dims, w["seed"])
     half_in = syn.to_half(psi, 1)
     si, so = q.Spinor(lat, "odd", "f64"), q.Spinor(lat, "even", "f64")
@@ -329,7 +326,27 @@ def test_dslash_full_size_sampled(q, name):
     assert F.rel_err(got, want) <= 1e-13
     # every output finite, and the norm consistent with a random field
     assert np.all(np.isfinite(out))
-    del g, lat
+
+
+def test_solve_48x12_twisted_full_size(q):
+    """The 48^3 x 12 twisted-mass workload (kappa 0.16, mu 0.01) at full size,
+    as the bench runs it: the FP16 mixed solve and the FP64 solve both reach
+    1e-10, the oracle's recomputed Schur residual of the GPU solution agrees,
+    and the two solutions match."""
+    w = syn.WORKLOADS["48^3x12"]
+    dims, kappa, mu = w["dims"], w["kappa"], w["mu"]
+    lat, U, g = gauge(q, dims, eps=w["eps"], seed=w["seed"])
+    b = syn.gaussian_spinor(dims, w["seed"] + 1)
+    bs = q.Spinor(lat, "full", "f64")
+    bs.upload(b)
+    xs = {}
+    for inner in ("f16", "f64"):
+        x = q.Spinor(lat, "full", "f64")
+        status, st = q.solve_cg(g, x, bs, kappa, mu, tol=1e-10, inner_prec=inner)
+        assert status == 0 and st["true_rel_residual"] <= 1e-10, (inner, st)
+        xs[inner] = x.download()
+    assert schur_residual_oracle(U, b, xs["f16"], kappa, mu) <= 1.5e-10
+    assert F.rel_err(xs["f16"], xs["f64"]) <= 1e-8
 
 
 def test_solve_eo_24x8_true_residual(q):
