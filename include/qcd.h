@@ -276,6 +276,18 @@ qcd_status qcd_solve_cg(const qcd_gauge *g, qcd_spinor *x, const qcd_spinor *b, 
 qcd_status qcd_solve_cg_multi(const qcd_gauge *g, qcd_spinor *const *x, const qcd_spinor *const *b, int nrhs,
                               const qcd_solver_params *params, qcd_solver_stats *stats, void *stream);
 
+/* n (1..32) systems that share the gauge field but have their own hopping
+ * parameter, twisted mass and tolerance -- params[k] for system k -- solved
+ * by one batched CG, as qcd_solve_cg_multi (batching over sources and kappa
+ * values).  All kappa/mu-dependent epilogue coefficients are read per
+ * right-hand side from a device table.  params[k].maxiter, eo, normal,
+ * inner_prec, inner_recon and reliable_delta must be the same for every k
+ * (INVALID_ARG otherwise); systems that converge first stop changing while
+ * the rest continue, and a reliable update of one is a reliable update of
+ * all.  Errors as for qcd_solve_cg_multi. */
+qcd_status qcd_solve_cg_batch(const qcd_gauge *g, qcd_spinor *const *x, const qcd_spinor *const *b, int n,
+                              const qcd_solver_params *params, qcd_solver_stats *stats, void *stream);
+
 /* ----------------------------------------------------------------- server */
 
 /* A solve server: independent even-odd CG solves of different volumes and

@@ -452,6 +452,7 @@ cudaError_t hop(const qcd_lattice *lat, const GaugeView &U, int recon, const Hop
     memcpy(a.cy, h.cy.c, sizeof(a.cy));
     memcpy(a.cd, h.cd.c, sizeof(a.cd));
     a.coef = h.coef;
+    a.coef_stride = h.coef_stride;
     if (h.plain)
         a.epi = EPI_PLAIN;
     else if (!h.y)
@@ -603,6 +604,7 @@ qcd_status qcd_lattice_create(const int dims[4], int t_bc, qcd_lattice **out)
     if (e == cudaSuccess) e = cudaMalloc(&lat->red_out_big, 2 * kMaxRhs * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&lat->state, sizeof(CgState));
     if (e == cudaSuccess) e = cudaMallocHost(&lat->state_host, sizeof(CgState));
+    if (e == cudaSuccess) e = cudaMallocHost(&lat->coef_host, kCoefHostDoubles * sizeof(double));
     if (e == cudaSuccess) e = cudaMemset(lat->red_counter, 0, 64);
     if (e == cudaSuccess) e = cudaMemset(lat->state, 0, sizeof(CgState));
     if (e != cudaSuccess) {
@@ -626,6 +628,7 @@ void qcd_lattice_destroy(qcd_lattice *lat)
     cudaFree(lat->red_out_big);
     cudaFree(lat->state);
     if (lat->state_host) cudaFreeHost(lat->state_host);
+    if (lat->coef_host) cudaFreeHost(lat->coef_host);
     for (auto &kv : lat->ws) cudaFree(kv.second.first);
     for (auto &kv : lat->graphs) {
         cudaGraphExecDestroy(kv.second.exec);

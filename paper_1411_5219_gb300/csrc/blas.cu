@@ -77,12 +77,18 @@ __global__ void __launch_bounds__(kThreads) zero_kernel(const FieldView f)
 
 template <typename SF>
 __global__ void __launch_bounds__(kThreads) twist_kernel(const FieldView out, const FieldView in, const double cr0,
-                                                         const double ci0, const double cr1, const double ci1)
+                                                         const double ci0, const double cr1, const double ci1,
+                                                         const double *table, const int stride)
 {
     using R = typename SF::R;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nsites(out)) return;
-    const cx<R> c[2] = {mk((R)cr0, (R)ci0), mk((R)cr1, (R)ci1)};
+    cx<R> c[2] = {mk((R)cr0, (R)ci0), mk((R)cr1, (R)ci1)};
+    if (table) {  // per-rhs coefficients
+        const double *t = table + (size_t)(k & ((1 << out.rhs_log2) - 1)) * stride;
+        c[0] = mk((R)t[0], (R)t[1]);
+        c[1] = mk((R)t[2], (R)t[3]);
+    }
     Spinor<R> a = ld<SF>(in, k);
 #pragma unroll
     for (int s = 0; s < 4; ++s)
@@ -120,17 +126,18 @@ __global__ void __launch_bounds__(kThreads) diff_norm2_kernel(const FieldView a,
     grid_reduce_rhs<2>(v, a.rhs_log2, red, FIN_STORE, nullptr, out);
 }
 
-__global__ void cg_state_init_kernel(CgState *s, int nrhs, double tol2, double delta2, int maxiter)
+__global__ void cg_state_init_kernel(CgState *s, int nrhs, const RhsValues tol2, double delta2, int maxiter)
 {
     for (int k = 0; k < kMaxRhs; ++k) {
         CgRhs &q = s->r[k];
         q.rr = q.rr_prev = q.pAp = q.alpha = q.beta = 0.0;
         q.rr_stop = q.rr_max = q.rr_true = q.b2 = 0.0;
+        q.tol2 = tol2.v[k];
         q.status = CG_DONE;
         q.iter_done = 0;
     }
     s->nrhs = nrhs;
-    s->tol2 = tol2;
+    s->tol2 = tol2.v[0];
     s->delta2 = delta2;
     s->iter = 0;
     s->maxiter = maxiter;
@@ -140,11 +147,6 @@ __global__ void cg_state_init_kernel(CgState *s, int nrhs, double tol2, double d
     s->trip_limit = maxiter + 64;
 }
 
-__global__ void set_table_kernel(double *dst, const CoefTable t)
-{
-    const int k = threadIdx.x;
-    if (k < t.n) dst[k] = t.v[k];
-}
 
 // Graph control: run the reliable-update body when the iteration asked for it.
 __global__ void cg_ctrl_reliable_kernel(const CgState *st, cudaGraphConditionalHandle h)
@@ -345,10 +347,12 @@ cudaError_t launch_zero(const FieldView &f, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_twist(const FieldView &out, const FieldView &in, const double c[2][2], cudaStream_t s)
+cudaError_t launch_twist(const FieldView &out, const FieldView &in, const double c[2][2], cudaStream_t s,
+                         const double *table, int stride)
 {
     if (out.prec != in.prec) return cudaErrorInvalidValue;
-    QCD_SP_CASES(out.prec, SF, twist_kernel<SF><<<grid_of(out), kThreads, 0, s>>>(out, in, c[0][0], c[0][1], c[1][0], c[1][1]));
+    QCD_SP_CASES(out.prec, SF, twist_kernel<SF><<<grid_of(out), kThreads, 0, s>>>(out, in, c[0][0], c[0][1], c[1][0], c[1][1],
+                                                                                 table, stride));
     note_launches();
     return cudaGetLastError();
 }
@@ -371,19 +375,14 @@ cudaError_t launch_diff_norm2(const FieldView &a, const FieldView &b, const Redu
     return cudaGetLastError();
 }
 
-cudaError_t launch_cg_state_init(CgState *stt, int nrhs, double tol2, double delta2, int maxiter, cudaStream_t s)
+cudaError_t launch_cg_state_init(CgState *stt, int nrhs, const RhsValues &tol2, double delta2, int maxiter,
+                                 cudaStream_t s)
 {
     cg_state_init_kernel<<<1, 1, 0, s>>>(stt, nrhs, tol2, delta2, maxiter);
     note_launches();
     return cudaGetLastError();
 }
 
-cudaError_t launch_set_table(double *dst, const CoefTable &t, cudaStream_t s)
-{
-    set_table_kernel<<<1, 64, 0, s>>>(dst, t);
-    note_launches();
-    return cudaGetLastError();
-}
 
 cudaError_t launch_cg_ctrl_reliable(const CgState *stt, cudaGraphConditionalHandle h, cudaStream_t s)
 {

@@ -259,11 +259,13 @@ __global__ void __launch_bounds__(TPB, (dslash_min_blocks_tpb<SF, GF, TPB>())) d
         // epilogue coefficients: kernel parameters, or a device table shared
         // by every launch of a captured CG graph (so one graph serves all
         // kappa and mu)
+        // (with a per-rhs table, the one of this element's rhs)
+        const double *cf = a.coef ? a.coef + (size_t)rhs * a.coef_stride : nullptr;
         double cyv[2][2], cdv[2][2];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            cyv[k >> 1][k & 1] = a.coef ? __ldg(a.coef + k) : a.cy[k >> 1][k & 1];
-            cdv[k >> 1][k & 1] = a.coef ? __ldg(a.coef + 4 + k) : a.cd[k >> 1][k & 1];
+            cyv[k >> 1][k & 1] = cf ? __ldg(cf + k) : a.cy[k >> 1][k & 1];
+            cdv[k >> 1][k & 1] = cf ? __ldg(cf + 4 + k) : a.cd[k >> 1][k & 1];
         }
         // epilogue
         Spinor<R> out;

@@ -8,6 +8,9 @@
 
 #include "qcd_ops.h"
 
+// Doubles of the pinned coefficient staging buffer: 96 per rhs, up to 32 rhs.
+constexpr int kCoefHostDoubles = 96 * 32;
+
 struct qcd_lattice {
     int dims[4];
     int t_bc;
@@ -24,6 +27,7 @@ struct qcd_lattice {
     double *red_out_big = nullptr;   // per-rhs FIN_STORE results (2 * kMaxRhs doubles)
     qcd::CgState *state = nullptr;   // device CG state
     qcd::CgState *state_host = nullptr;  // pinned mirror
+    double *coef_host = nullptr;         // pinned staging of a solve's coefficient table (kCoefHostDoubles)
     // Named workspace buffers (staging, solver fields), grown on demand.
     mutable std::map<std::string, std::pair<void *, size_t>> ws;
     // Instantiated CG-loop graphs keyed by solver configuration and field
@@ -118,11 +122,14 @@ struct HopArgs {
     bool check_status;
     const Reduction *red;  // scratch of the fused reduction (nullptr: the lattice's)
     const double *coef;    // device table of cy, cd (8 doubles) read at run time, or nullptr
+    int coef_stride;       // doubles between the tables of consecutive rhs (0: shared)
 };
 cudaError_t hop(const qcd_lattice *lat, const GaugeView &U, int recon, const HopArgs &h, cudaStream_t s);
 
 // The CG solve behind qcd_solve_cg / qcd_solve_cg_multi, with an optional
 // context lattice (scratch, state, graphs) other than the gauge field's.
+// prm holds one parameter set per right-hand side (kappa, mu and tol may
+// differ; the other fields must agree).
 qcd_status solve_impl(const qcd_gauge *g, qcd_spinor *const *x, const qcd_spinor *const *b, int nrhs,
                       const qcd_solver_params *prm, qcd_solver_stats *stats, cudaStream_t s, const qcd_lattice *ctx);
 

@@ -853,6 +853,7 @@ struct CgRhs {
     double rr_max;    // largest |r|^2 since the last reliable update
     double rr_true;   // |rhs - A x|^2 of the last true-residual computation
     double b2;        // |rhs|^2
+    double tol2;      // this rhs's target relative residual, squared
     int status;       // RUNNING, DONE or BREAKDOWN
     int iter_done;    // iteration at which it was solved
 };
@@ -887,7 +888,7 @@ __device__ __forceinline__ void cg_finalize_rhs(FinalizeKind kind, const double 
             CgRhs &q = st->r[k];
             const double b2 = tot[k];
             q.rr = q.rr_prev = q.rr_max = q.rr_true = q.b2 = b2;
-            q.rr_stop = st->tol2 * b2;
+            q.rr_stop = q.tol2 * b2;
             q.alpha = q.beta = q.pAp = 0.0;
             q.iter_done = 0;
             q.status = b2 == 0.0 ? CG_DONE : CG_RUNNING;
@@ -1077,6 +1078,7 @@ struct DslashLaunch {
     SpinorView in[2], out[2], y[2];
     double cy[2][2], cd[2][2];  // [chirality][re, im]
     const double *coef;         // if set: cy, cd read from this device table (8 doubles) instead
+    int coef_stride;            // doubles between the tables of consecutive rhs (0: one table for all)
     EpiMode epi;
     // optional fused |out|^2 reduction
     bool reduce;

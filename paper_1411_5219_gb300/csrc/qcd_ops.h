@@ -19,7 +19,9 @@ struct FieldView {
 };
 
 // out = c[chi] * in (one complex factor per chirality), e.g. A^-1 psi.
-cudaError_t launch_twist(const FieldView &out, const FieldView &in, const double c[2][2], cudaStream_t s);
+// out = c[chirality] in; with `table`, rhs r takes its c from table + r * stride (4 doubles).
+cudaError_t launch_twist(const FieldView &out, const FieldView &in, const double c[2][2], cudaStream_t s,
+                         const double *table = nullptr, int stride = 0);
 // dst = src with precision conversion.
 cudaError_t launch_convert(const FieldView &dst, const FieldView &src, cudaStream_t s);
 cudaError_t launch_zero(const FieldView &f, cudaStream_t s);
@@ -32,7 +34,12 @@ cudaError_t launch_diff_norm2(const FieldView &a, const FieldView &b, const Redu
 
 // CG vector steps.  The CG state lives on the device; every kernel below
 // except cg_true_residual returns at once unless state->status is RUNNING.
-cudaError_t launch_cg_state_init(CgState *st, int nrhs, double tol2, double delta2, int maxiter, cudaStream_t s);
+// One double per right-hand side (kernel parameter).
+struct RhsValues {
+    double v[kMaxRhs];
+};
+cudaError_t launch_cg_state_init(CgState *st, int nrhs, const RhsValues &tol2, double delta2, int maxiter,
+                                 cudaStream_t s);
 // r = rhs (cast), p = r, x = 0, xs = 0 (if given); rr = |rhs|^2; status.
 cudaError_t launch_cg_setup(const FieldView &rhs, const FieldView &r, const FieldView &p, const FieldView &x,
                             const FieldView *xs, const Reduction &red, CgState *st, cudaStream_t s);
@@ -48,12 +55,6 @@ cudaError_t launch_cg_accum_x(const FieldView &xhi, const FieldView &xs, cudaStr
 cudaError_t launch_cg_true_residual(const FieldView &rhs, const FieldView &q, const FieldView &rhi,
                                    const FieldView *rs, const Reduction &red, CgState *st, cudaStream_t s);
 
-// Small table of doubles written on the stream (kernel parameters -> device).
-struct CoefTable {
-    double v[64];
-    int n;
-};
-cudaError_t launch_set_table(double *dst, const CoefTable &t, cudaStream_t s);
 
 // Graph control kernels (cudaGraphSetConditional on the loop / reliable-update handles).
 cudaError_t launch_cg_ctrl_reliable(const CgState *st, cudaGraphConditionalHandle h, cudaStream_t s);

@@ -33,33 +33,64 @@ namespace {
 
 struct OpCtx {
     const qcd_lattice *lat;
-    double kappa, a;  // a = 2 kappa mu
+    bool tw;               // some right-hand side has mu != 0 (complex chiral coefficients)
     bool eo;
     const Reduction *red;  // scratch of the fused |Mhat p|^2 reduction
-    const double *coef;    // device table of the normal operator's epilogue coefficients (4 x 8), or nullptr
+    const double *coef;    // device table of the epilogue coefficients, kCoefPerRhs doubles per rhs
 };
 
-// Epilogue coefficients of the normal operator's hops (see apply_normal),
-// 8 doubles each (cy[2][2], cd[2][2]).
-CoefTable normal_op_table(const OpCtx &c)
+// Per right-hand side, the solve reads every kappa- and mu-dependent
+// coefficient from one device table, so a batch may mix kappa and mu values
+// and the cached CG graph depends on neither.  Blocks of 8 doubles
+// (cy[2][2], cd[2][2]) at these offsets:
+constexpr int kCoefPerRhs = 96;
+constexpr int kCoefOp = 0;        // normal operator, 4 hops (2 for the full lattice)
+constexpr int kCoefSrcB = 32;     // b' = b_e + kappa D_eo A^-1 b_o
+constexpr int kCoefSrcT = 40;     // t = A^-dag D_oe^dag b'
+constexpr int kCoefSrcR = 48;     // rhs = A^dag b' - kappa^2 D_eo^dag t
+constexpr int kCoefRecon = 56;    // x_o = A^-1 b_o + kappa A^-1 D_oe x_e
+constexpr int kCoefFullM = 64;    // M = A - kappa D
+constexpr int kCoefFullMd = 72;   // M^dag
+constexpr int kCoefTwistInv = 80; // A^-1 (4 doubles: one complex per chirality)
+
+void put_coef(double *t, int off, const Coef &cy, const Coef &cd)
 {
-    CoefTable t{};
-    auto put = [&](int k, const Coef &cy, const Coef &cd) {
-        memcpy(t.v + 8 * k, cy.c, 4 * sizeof(double));
-        memcpy(t.v + 8 * k + 4, cd.c, 4 * sizeof(double));
-    };
+    memcpy(t + off, cy.c, 4 * sizeof(double));
+    memcpy(t + off + 4, cd.c, 4 * sizeof(double));
+}
+
+// The coefficient block of one right-hand side with hopping parameter
+// kappa and a = 2 kappa mu.
+void coef_block(double *t, bool eo, double kappa, double a)
+{
     const Coef zero = coef_real(0.0);
-    if (c.eo) {
-        put(0, zero, coef_twist_inv(c.a));
-        put(1, coef_twist(c.a), coef_real(-c.kappa * c.kappa));
-        put(2, zero, coef_twist_inv(-c.a));
-        put(3, coef_twist(-c.a), coef_real(-c.kappa * c.kappa));
+    if (eo) {
+        put_coef(t, kCoefOp + 0, zero, coef_twist_inv(a));
+        put_coef(t, kCoefOp + 8, coef_twist(a), coef_real(-kappa * kappa));
+        put_coef(t, kCoefOp + 16, zero, coef_twist_inv(-a));
+        put_coef(t, kCoefOp + 24, coef_twist(-a), coef_real(-kappa * kappa));
     } else {
-        put(0, coef_twist(c.a), coef_real(-c.kappa));
-        put(1, coef_twist(-c.a), coef_real(-c.kappa));
+        put_coef(t, kCoefOp + 0, coef_twist(a), coef_real(-kappa));
+        put_coef(t, kCoefOp + 8, coef_twist(-a), coef_real(-kappa));
     }
-    t.n = 32;
-    return t;
+    put_coef(t, kCoefSrcB, coef_real(1.0), coef_real(kappa));
+    put_coef(t, kCoefSrcT, zero, coef_twist_inv(-a));
+    put_coef(t, kCoefSrcR, coef_twist(-a), coef_real(-kappa * kappa));
+    put_coef(t, kCoefRecon, coef_twist_inv(a), coef_scale(coef_twist_inv(a), kappa));
+    put_coef(t, kCoefFullM, coef_twist(a), coef_real(-kappa));
+    put_coef(t, kCoefFullMd, coef_twist(-a), coef_real(-kappa));
+    const Coef ti = coef_twist_inv(a);
+    memcpy(t + kCoefTwistInv, ti.c, 4 * sizeof(double));
+}
+
+// A hop whose epilogue coefficients come from block `off` of the table.
+HopArgs table_hop(const OpCtx &c, int off)
+{
+    HopArgs h{};
+    h.coef = c.coef + off;
+    h.coef_stride = kCoefPerRhs;
+    h.twisted = c.tw;
+    return h;
 }
 
 // out = Mhat^dag Mhat in (eo) or M^dag M in (full).  t (odd half) and s
@@ -68,42 +99,33 @@ CoefTable normal_op_table(const OpCtx &c)
 cudaError_t apply_normal(const OpCtx &c, const GaugeView &U, int recon, const FieldView &in, const FieldView &out,
                          const FieldView &t, const FieldView &s, bool reduce_alpha, bool check, cudaStream_t st)
 {
-    const bool tw = c.a != 0.0;
     cudaError_t e;
     if (c.eo) {
-        HopArgs h{};
+        // t = A^-1 D_oe in
+        HopArgs h = table_hop(c, kCoefOp + 0);
         h.check_status = check;
         h.fin = FIN_CG_ALPHA;
-        // t = A^-1 D_oe in
         h.out = &t;
         h.in = &in;
         h.out_parity = 1;
-        h.plain = !tw;
-        h.twisted = tw;
-        h.cd = coef_twist_inv(c.a);
-        h.coef = c.coef;
+        h.plain = !c.tw;
         if ((e = hop(c.lat, U, recon, h, st)) != cudaSuccess) return e;
         // s = A in - kappa^2 D_eo t   (|s|^2 -> alpha)
-        HopArgs h2{};
+        HopArgs h2 = table_hop(c, kCoefOp + 8);
         h2.check_status = check;
         h2.fin = FIN_CG_ALPHA;
         h2.out = &s;
         h2.in = &t;
         h2.y = &in;
         h2.out_parity = 0;
-        h2.twisted = tw;
-        h2.cy = coef_twist(c.a);
-        h2.cd = coef_real(-c.kappa * c.kappa);
         h2.reduce = reduce_alpha;
         h2.red = c.red;
-        h2.coef = c.coef ? c.coef + 8 : nullptr;
         if ((e = hop(c.lat, U, recon, h2, st)) != cudaSuccess) return e;
         // t = A^-dag D_oe^dag s
         HopArgs h3 = h;
         h3.in = &s;
         h3.dagger = 1;
-        h3.cd = coef_twist_inv(-c.a);
-        h3.coef = c.coef ? c.coef + 16 : nullptr;
+        h3.coef = c.coef + kCoefOp + 16;
         if ((e = hop(c.lat, U, recon, h3, st)) != cudaSuccess) return e;
         // out = A^dag s - kappa^2 D_eo^dag t
         HopArgs h4 = h2;
@@ -111,25 +133,20 @@ cudaError_t apply_normal(const OpCtx &c, const GaugeView &U, int recon, const Fi
         h4.in = &t;
         h4.y = &s;
         h4.dagger = 1;
-        h4.cy = coef_twist(-c.a);
         h4.reduce = false;
-        h4.coef = c.coef ? c.coef + 24 : nullptr;
+        h4.coef = c.coef + kCoefOp + 24;
         return hop(c.lat, U, recon, h4, st);
     }
     // s = M in = A in - kappa D in  (|s|^2 -> alpha)
-    HopArgs h{};
+    HopArgs h = table_hop(c, kCoefOp + 0);
     h.check_status = check;
     h.fin = FIN_CG_ALPHA;
     h.out = &s;
     h.in = &in;
     h.y = &in;
     h.both = true;
-    h.twisted = tw;
-    h.cy = coef_twist(c.a);
-    h.cd = coef_real(-c.kappa);
     h.reduce = reduce_alpha;
     h.red = c.red;
-    h.coef = c.coef;
     if ((e = hop(c.lat, U, recon, h, st)) != cudaSuccess) return e;
     // out = M^dag s
     HopArgs h2 = h;
@@ -137,9 +154,8 @@ cudaError_t apply_normal(const OpCtx &c, const GaugeView &U, int recon, const Fi
     h2.in = &s;
     h2.y = &s;
     h2.dagger = 1;
-    h2.cy = coef_twist(-c.a);
     h2.reduce = false;
-    h2.coef = c.coef ? c.coef + 8 : nullptr;
+    h2.coef = c.coef + kCoefOp + 8;
     return hop(c.lat, U, recon, h2, st);
 }
 
@@ -147,16 +163,13 @@ cudaError_t apply_normal(const OpCtx &c, const GaugeView &U, int recon, const Fi
 cudaError_t apply_full_m(const OpCtx &c, const GaugeView &U, int recon, const FieldView &in, const FieldView &out,
                          int dagger, cudaStream_t st)
 {
-    HopArgs h{};
+    HopArgs h = table_hop(c, dagger ? kCoefFullMd : kCoefFullM);
     h.fin = FIN_STORE;
     h.out = &out;
     h.in = &in;
     h.y = &in;
     h.both = true;
     h.dagger = dagger;
-    h.twisted = c.a != 0.0;
-    h.cy = coef_twist(dagger ? -c.a : c.a);
-    h.cd = coef_real(-c.kappa);
     return hop(c.lat, U, recon, h, st);
 }
 
@@ -259,7 +272,7 @@ qcd_status cg_graph(const qcd_lattice *lat, const CgFields &f, cudaGraphExec_t *
 {
     char key[512];
     snprintf(key, sizeof(key), "%d|%d|%p|%d|%d|%d|%p|%p|%p|%p|%p|%p|%p|%p|%p|%p|%p|%p|%p|%p|%d|%d", (int)f.c.eo,
-             (int)(f.c.a != 0.0), (const void *)f.c.coef, (int)f.mixed, f.rh_recon, f.rs_recon, f.Uh.data, f.Us.data, f.rhs.hv[0].data,
+             (int)f.c.tw, (const void *)f.c.coef, (int)f.mixed, f.rh_recon, f.rs_recon, f.Uh.data, f.Us.data, f.rhs.hv[0].data,
              f.xh.hv[0].data, f.xh.hv[1].data, f.rh.hv[0].data, f.qh.hv[0].data, f.th.hv[0].data, f.sh.hv[0].data,
              f.rs.hv[0].data, f.ps.hv[0].data, f.qs.hv[0].data, f.ts.hv[0].data, f.ss.hv[0].data, f.xs.hv[0].data,
              (void *)f.state, f.rs.prec, f.rhs.nh);
@@ -402,8 +415,16 @@ qcd_status qcd::solve_impl(const qcd_gauge *g, qcd_spinor *const *x, const qcd_s
         if (x[k]->ks || b[k]->ks) return fail(QCD_ERR_INVALID_ARG, "solve_cg: staggered fields are not solved here");
     }
     if (g->prec != QCD_PREC_F64) return fail(QCD_ERR_INVALID_ARG, "solve_cg: the gauge field must be F64");
-    if (!(prm->tol > 0.0) || prm->maxiter < 1 || !std::isfinite(prm->kappa) || !std::isfinite(prm->mu))
-        return fail(QCD_ERR_INVALID_ARG, "solve_cg: bad tol/maxiter/kappa/mu");
+    for (int k = 0; k < nrhs; ++k) {
+        const qcd_solver_params &q = prm[k];
+        if (!(q.tol > 0.0) || q.maxiter < 1 || !std::isfinite(q.kappa) || !std::isfinite(q.mu))
+            return fail(QCD_ERR_INVALID_ARG, "solve_cg: bad tol/maxiter/kappa/mu (system %d)", k);
+        if (k > 0 && (q.maxiter != prm->maxiter || q.eo != prm->eo || q.normal != prm->normal ||
+                      q.inner_prec != prm->inner_prec || q.inner_recon != prm->inner_recon ||
+                      q.reliable_delta != prm->reliable_delta))
+            return fail(QCD_ERR_INVALID_ARG,
+                        "solve_cg: the systems of one batch may differ in kappa, mu and tol only (system %d)", k);
+    }
     if (prm->eo && prm->normal) return fail(QCD_ERR_INVALID_ARG, "solve_cg: normal = 1 needs eo = 0");
     if (prm->inner_prec < QCD_PREC_F64 || prm->inner_prec > QCD_PREC_DF64)
         return fail(QCD_ERR_INVALID_ARG, "solve_cg: bad inner_prec");
@@ -426,8 +447,9 @@ qcd_status qcd::solve_impl(const qcd_gauge *g, qcd_spinor *const *x, const qcd_s
     int L = 0;
     while ((1 << L) < nrhs) ++L;
     const int N = 1 << L;
-    OpCtx c{lat, prm->kappa, 2.0 * prm->kappa * prm->mu, prm->eo != 0, nullptr, nullptr};
-    const bool tw = c.a != 0.0;
+    bool tw = false;
+    for (int k = 0; k < nrhs; ++k) tw = tw || prm[k].mu != 0.0;
+    OpCtx c{lat, tw, prm->eo != 0, nullptr, nullptr};
     const int nh = c.eo ? 1 : 2;
 
     // b and x as (batched) full fields
@@ -451,12 +473,24 @@ qcd_status qcd::solve_impl(const qcd_gauge *g, qcd_spinor *const *x, const qcd_s
         if (!red.partials) return fail(QCD_ERR_OOM, "solve_cg: workspace");
     }
     c.red = &red;
-    // the normal operator's coefficients live in a device table, so the
-    // cached CG graph does not depend on kappa and mu
-    double *coef = static_cast<double *>(workspace(lat, "cg_coef", 64 * sizeof(double)));
+    // every kappa/mu-dependent coefficient lives in a device table (one block
+    // per rhs; padding rhs repeat system 0), so the cached CG graph depends
+    // on neither
+    double *coef = static_cast<double *>(workspace(lat, "cg_coef", (size_t)kMaxRhs * kCoefPerRhs * sizeof(double)));
     if (!coef) return fail(QCD_ERR_OOM, "solve_cg: workspace");
     c.coef = coef;
-    QCD_TRY(launch_set_table(coef, normal_op_table(c), s), "solve_cg: coefficients");
+    {
+        // staged in the lattice's pinned buffer: the previous solve on this
+        // lattice synchronised its stream before returning, so the buffer is free
+        static_assert(kCoefPerRhs * kMaxRhs <= kCoefHostDoubles, "coefficient staging buffer too small");
+        double *table = lat->coef_host;
+        for (int k = 0; k < N; ++k) {
+            const qcd_solver_params &q = prm[k < nrhs ? k : 0];
+            coef_block(table + (size_t)k * kCoefPerRhs, c.eo, q.kappa, 2.0 * q.kappa * q.mu);
+        }
+        QCD_TRY(cudaMemcpyAsync(coef, table, (size_t)N * kCoefPerRhs * sizeof(double), cudaMemcpyHostToDevice, s),
+                "solve_cg: coefficients");
+    }
 
     // FP64 fields
     FieldView rhs = c.eo ? ws_field(lat, "cg_rhs", 1, QCD_PREC_F64, L) : bf;
@@ -489,39 +523,33 @@ qcd_status qcd::solve_impl(const qcd_gauge *g, qcd_spinor *const *x, const qcd_s
         if (!bp.hv[0].data) return fail(QCD_ERR_OOM, "solve_cg: workspace");
         const FieldView *src = &bo;
         if (tw) {  // th = A^-1 b_o
-            const Coef ci = coef_twist_inv(c.a);
-            QCD_TRY(launch_twist(th, bo, ci.c, s), "solve_cg: source");
+            const double unused[2][2] = {{1.0, 0.0}, {1.0, 0.0}};
+            QCD_TRY(launch_twist(th, bo, unused, s, coef + kCoefTwistInv, kCoefPerRhs), "solve_cg: source");
             src = &th;
         }
-        HopArgs h{};  // b' = b_e + kappa D_eo (A^-1 b_o)
+        HopArgs h = table_hop(c, kCoefSrcB);  // b' = b_e + kappa D_eo (A^-1 b_o)
         h.fin = FIN_STORE;
         h.out = &bp;
         h.in = src;
         h.y = &be;
         h.out_parity = 0;
-        h.cy = coef_real(1.0);
-        h.cd = coef_real(c.kappa);
+        h.twisted = false;  // real coefficients 1 and kappa
         QCD_TRY(hop(lat, Uh, g->recon, h, s), "solve_cg: source");
-        HopArgs h3{};  // th = A^-dag D_oe^dag b'
+        HopArgs h3 = table_hop(c, kCoefSrcT);  // th = A^-dag D_oe^dag b'
         h3.fin = FIN_STORE;
         h3.out = &th;
         h3.in = &bp;
         h3.out_parity = 1;
         h3.dagger = 1;
         h3.plain = !tw;
-        h3.twisted = tw;
-        h3.cd = coef_twist_inv(-c.a);
         QCD_TRY(hop(lat, Uh, g->recon, h3, s), "solve_cg: source");
-        HopArgs h4{};  // rhs = A^dag b' - kappa^2 D_eo^dag th
+        HopArgs h4 = table_hop(c, kCoefSrcR);  // rhs = A^dag b' - kappa^2 D_eo^dag th
         h4.fin = FIN_STORE;
         h4.out = &rhs;
         h4.in = &th;
         h4.y = &bp;
         h4.out_parity = 0;
         h4.dagger = 1;
-        h4.twisted = tw;
-        h4.cy = coef_twist(-c.a);
-        h4.cd = coef_real(-c.kappa * c.kappa);
         QCD_TRY(hop(lat, Uh, g->recon, h4, s), "solve_cg: source");
     } else if (!prm->normal) {
         rhs = ws_field(lat, "cg_rhs", 2, QCD_PREC_F64, L);
@@ -532,7 +560,9 @@ qcd_status qcd::solve_impl(const qcd_gauge *g, qcd_spinor *const *x, const qcd_s
     // ---- CG
     CgFields F{c, Uh, Us, g->recon, srecon, mixed, rhs, xh, rh, qh, th, sh, rs, ps, qs, ts, ss, xs, red, lat->state};
     const double delta = mixed ? prm->reliable_delta : 0.0;
-    QCD_TRY(launch_cg_state_init(lat->state, N, prm->tol * prm->tol, delta * delta, prm->maxiter, s), "solve_cg: init");
+    RhsValues tol2{};
+    for (int k = 0; k < kMaxRhs; ++k) tol2.v[k] = prm[k < nrhs ? k : 0].tol * prm[k < nrhs ? k : 0].tol;
+    QCD_TRY(launch_cg_state_init(lat->state, N, tol2, delta * delta, prm->maxiter, s), "solve_cg: init");
     QCD_TRY(launch_cg_setup(rhs, rs, ps, xh, mixed ? &xs : nullptr, F.red, lat->state, s), "solve_cg: setup");
 
     qcd_status result = QCD_OK;
@@ -566,15 +596,12 @@ after_loop:
     // ---- odd sites and residuals
     if (c.eo) {
         const FieldView xo = half_of(xf, 1), bo = half_of(bf, 1);
-        HopArgs h{};  // x_o = A^-1 b_o + kappa A^-1 D_oe x_e
+        HopArgs h = table_hop(c, kCoefRecon);  // x_o = A^-1 b_o + kappa A^-1 D_oe x_e
         h.fin = FIN_STORE;
         h.out = &xo;
         h.in = &xh;
         h.y = &bo;
         h.out_parity = 1;
-        h.twisted = tw;
-        h.cy = coef_twist_inv(c.a);
-        h.cd = coef_scale(coef_twist_inv(c.a), c.kappa);
         QCD_TRY(hop(lat, Uh, g->recon, h, s), "solve_cg: reconstruct");
     }
     double true_rel[kMaxRhs], full_rel[kMaxRhs];
@@ -633,5 +660,14 @@ extern "C" qcd_status qcd_solve_cg_multi(const qcd_gauge *g, qcd_spinor *const *
                                          int nrhs, const qcd_solver_params *prm, qcd_solver_stats *stats,
                                          void *stream)
 {
-    return solve_impl(g, x, b, nrhs, prm, stats, static_cast<cudaStream_t>(stream), nullptr);
+    if (!prm) return fail(QCD_ERR_INVALID_ARG, "solve_cg_multi: NULL argument");
+    if (nrhs < 1 || nrhs > kMaxRhs) return fail(QCD_ERR_INVALID_ARG, "solve_cg_multi: nrhs = %d not in 1..%d", nrhs, kMaxRhs);
+    std::vector<qcd_solver_params> p((size_t)nrhs, *prm);
+    return solve_impl(g, x, b, nrhs, p.data(), stats, static_cast<cudaStream_t>(stream), nullptr);
+}
+
+extern "C" qcd_status qcd_solve_cg_batch(const qcd_gauge *g, qcd_spinor *const *x, const qcd_spinor *const *b, int n,
+                                         const qcd_solver_params *prm, qcd_solver_stats *stats, void *stream)
+{
+    return solve_impl(g, x, b, n, prm, stats, static_cast<cudaStream_t>(stream), nullptr);
 }

@@ -99,6 +99,8 @@ _SIGS = {
     "qcd_apply_dslash_multi": (_i, [_p, ctypes.POINTER(_p), ctypes.POINTER(_p), _i, _i, _p]),
     "qcd_solve_cg_multi": (_i, [_p, ctypes.POINTER(_p), ctypes.POINTER(_p), _i, ctypes.POINTER(SolverParams),
                                 ctypes.POINTER(SolverStats), _p]),
+    "qcd_solve_cg_batch": (_i, [_p, ctypes.POINTER(_p), ctypes.POINTER(_p), _i, ctypes.POINTER(SolverParams),
+                                ctypes.POINTER(SolverStats), _p]),
 }
 
 _lib = None
@@ -338,6 +340,28 @@ def solve_cg_multi(gauge: Gauge, xs, bs, kappa: float, mu: float = 0.0, tol: flo
                                       _stream(stream))
     if raise_on_error and status != 0:
         _check(status, "qcd_solve_cg_multi")
+    return status, [{k: getattr(st[i], k) for k, _ in SolverStats._fields_} for i in range(n)]
+
+
+def solve_cg_batch(gauge: Gauge, xs, bs, kappas, mus=None, tols=None, maxiter: int = 20000, eo: bool = True,
+                   normal: bool = False, inner_prec: str = "f64", inner_recon: int = 12, reliable_delta: float = 0.1,
+                   stream=None, raise_on_error: bool = True):
+    """Batched CG over systems with their own kappa, mu and tol (qcd_solve_cg_batch);
+    returns (status, [stats dict])."""
+    n = len(bs)
+    if len(xs) != n or len(kappas) != n:
+        raise ValueError("xs, bs and kappas differ in length")
+    mus = [0.0] * n if mus is None else list(mus)
+    tols = [1e-10] * n if tols is None else list(tols)
+    if len(mus) != n or len(tols) != n:
+        raise ValueError("mus / tols differ in length from bs")
+    prm = (SolverParams * n)(*[SolverParams(float(kappas[k]), float(mus[k]), float(tols[k]), int(maxiter),
+                                            int(bool(eo)), int(bool(normal)), PREC[inner_prec], int(inner_recon),
+                                            float(reliable_delta)) for k in range(n)])
+    st = (SolverStats * n)()
+    status = lib().qcd_solve_cg_batch(gauge.handle, _handles(xs), _handles(bs), n, prm, st, _stream(stream))
+    if raise_on_error and status != 0:
+        _check(status, "qcd_solve_cg_batch")
     return status, [{k: getattr(st[i], k) for k, _ in SolverStats._fields_} for i in range(n)]
 
 
