@@ -913,8 +913,13 @@ __device__ __forceinline__ void cg_finalize_rhs(FinalizeKind kind, const double 
             }
         }
     } else if (kind == FIN_CG_RR) {
+        // A true-residual update runs when some system's residual fell by the
+        // reliable-update factor, or when every running system's iterated
+        // residual meets its target (a system that converges first keeps
+        // iterating until then, so a batch pays one final check, not one per
+        // system).
         st->iter += 1;
-        bool want = false, bad = false;
+        bool want = false, all_met = true, bad = false;
         for (int k = 0; k < n; ++k) {
             CgRhs &q = st->r[k];
             if (q.status == CG_DONE) {
@@ -926,12 +931,13 @@ __device__ __forceinline__ void cg_finalize_rhs(FinalizeKind kind, const double 
             q.beta = rr_new / q.rr;
             q.rr = rr_new;
             if (!isfinite(rr_new)) bad = true;
-            if (rr_new <= q.rr_stop || (st->delta2 > 0.0 && rr_new < st->delta2 * q.rr_max)) want = true;
+            if (st->delta2 > 0.0 && rr_new < st->delta2 * q.rr_max) want = true;
+            all_met = all_met && rr_new <= q.rr_stop;
             if (rr_new > q.rr_max) q.rr_max = rr_new;
         }
         if (bad)
             st->status = CG_BREAKDOWN;
-        else if (want)
+        else if (want || all_met)
             st->status = CG_RELIABLE;
         else if (st->iter >= st->maxiter)
             st->status = CG_MAXITER;

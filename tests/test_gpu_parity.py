@@ -578,8 +578,10 @@ def test_solve_batch_mixed_kappa_mu_tol(q, inner):
         x1 = q.Spinor(lat, "full", "f64")
         q.solve_cg(g, x1, bs[k], kappas[k], mus[k], tol=tols[k], inner_prec=inner)
         assert F.rel_err(xb, x1.download()) <= 1e3 * tols[k], k
-    # the faster-converging systems are solved at earlier iterations
-    assert stats[0]["iterations"] < stats[3]["iterations"]
+    if inner == "f64":
+        # systems that meet their tolerance early keep iterating until all have:
+        # the FP64 batch pays one true-residual check, not one per system
+        assert all(s_["reliable_updates"] == 1 for s_ in stats)
 
 
 def test_solve_batch_rejects_mixed_settings(q):
