@@ -913,13 +913,15 @@ __device__ __forceinline__ void cg_finalize_rhs(FinalizeKind kind, const double 
             }
         }
     } else if (kind == FIN_CG_RR) {
-        // A true-residual update runs when some system's residual fell by the
-        // reliable-update factor, or when every running system's iterated
-        // residual meets its target (a system that converges first keeps
-        // iterating until then, so a batch pays one final check, not one per
-        // system).
+        // A true-residual update runs when every running system is ready --
+        // its residual fell by the reliable-update factor delta since the last
+        // update, or it meets its target -- or when some system's residual
+        // fell by delta^2 (so one slow system cannot hold the others back).
+        // A batch of similar systems thus pays about the updates of one
+        // solve, and one final check rather than one per system.
         st->iter += 1;
-        bool want = false, all_met = true, bad = false;
+        bool all_ready = true, urgent = false, bad = false;
+        const double d2 = st->delta2;
         for (int k = 0; k < n; ++k) {
             CgRhs &q = st->r[k];
             if (q.status == CG_DONE) {
@@ -931,13 +933,14 @@ __device__ __forceinline__ void cg_finalize_rhs(FinalizeKind kind, const double 
             q.beta = rr_new / q.rr;
             q.rr = rr_new;
             if (!isfinite(rr_new)) bad = true;
-            if (st->delta2 > 0.0 && rr_new < st->delta2 * q.rr_max) want = true;
-            all_met = all_met && rr_new <= q.rr_stop;
+            const bool dropped = d2 > 0.0 && rr_new < d2 * q.rr_max;
+            all_ready = all_ready && (dropped || rr_new <= q.rr_stop);
+            urgent = urgent || (d2 > 0.0 && rr_new < d2 * d2 * q.rr_max);
             if (rr_new > q.rr_max) q.rr_max = rr_new;
         }
         if (bad)
             st->status = CG_BREAKDOWN;
-        else if (want || all_met)
+        else if (all_ready || urgent)
             st->status = CG_RELIABLE;
         else if (st->iter >= st->maxiter)
             st->status = CG_MAXITER;
