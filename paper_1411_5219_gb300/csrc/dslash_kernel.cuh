@@ -123,6 +123,72 @@ __device__ __forceinline__ HalfSpinor<R> su3_mul(const Link<R> &u, const HalfSpi
     return r;
 }
 
+// seed + U h (kAdj = false) or seed + U^dagger h (kAdj = true): the
+// product's multiply-add chains start from the seed.
+template <typename R, bool kAdj>
+__device__ __forceinline__ HalfSpinor<R> su3_mul_seeded(const Link<R> &u, const HalfSpinor<R> &h,
+                                                        const HalfSpinor<R> &seed)
+{
+    HalfSpinor<R> r;
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            cx<R> v = seed.c[s][a];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) v = kAdj ? cjmac(v, u.m[j][a], h.c[s][j]) : cmac(v, u.m[a][j], h.c[s][j]);
+            r.c[s][a] = v;
+        }
+    return r;
+}
+
+// Both hops of direction mu at once (FP64 kernels): with u_f = U h_f of
+// the forward hop and u_b = U^dagger h_b of the backward one, the upper spins
+// gain s = u_f + u_b and the lower spins phi pi(u_f - u_b), since the two
+// hops' rebuild phases differ only in sign.  s comes from the backward
+// product's chains seeded with u_f, and u_f - u_b = 2 u_f - s, which saves
+// the separate additions of one hop.
+template <typename R, int MU, int S, bool kFirst>
+__device__ __forceinline__ void accumulate_pair(Spinor<R> &acc, const HalfSpinor<R> &uf, const HalfSpinor<R> &sum)
+{
+    HalfSpinor<R> d;
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            d.c[s][c].re = fma(R(2), uf.c[s][c].re, -sum.c[s][c].re);
+            d.c[s][c].im = fma(R(2), uf.c[s][c].im, -sum.c[s][c].im);
+        }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        cx<R> l2, l3;
+        if (MU == 0) {  // -S (i d1, i d0)
+            l2 = S > 0 ? -ti(d.c[1][c]) : ti(d.c[1][c]);
+            l3 = S > 0 ? -ti(d.c[0][c]) : ti(d.c[0][c]);
+        } else if (MU == 1) {  // -S (d1, -d0)
+            l2 = S > 0 ? -d.c[1][c] : d.c[1][c];
+            l3 = S > 0 ? d.c[0][c] : -d.c[0][c];
+        } else if (MU == 2) {  // -S (i d0, -i d1)
+            l2 = S > 0 ? -ti(d.c[0][c]) : ti(d.c[0][c]);
+            l3 = S > 0 ? ti(d.c[1][c]) : -ti(d.c[1][c]);
+        } else {  // -S (d0, d1)
+            l2 = S > 0 ? -d.c[0][c] : d.c[0][c];
+            l3 = S > 0 ? -d.c[1][c] : d.c[1][c];
+        }
+        if (kFirst) {
+            acc.c[0][c] = sum.c[0][c];
+            acc.c[1][c] = sum.c[1][c];
+            acc.c[2][c] = l2;
+            acc.c[3][c] = l3;
+        } else {
+            acc.c[0][c] = acc.c[0][c] + sum.c[0][c];
+            acc.c[1][c] = acc.c[1][c] + sum.c[1][c];
+            acc.c[2][c] = acc.c[2][c] + l2;
+            acc.c[3][c] = acc.c[3][c] + l3;
+        }
+    }
+}
+
 template <typename R>
 __device__ __forceinline__ void negate(HalfSpinor<R> &h)
 {
@@ -130,6 +196,29 @@ __device__ __forceinline__ void negate(HalfSpinor<R> &h)
     for (int s = 0; s < 2; ++s)
 #pragma unroll
         for (int c = 0; c < 3; ++c) h.c[s][c] = -h.c[s][c];
+}
+
+// The forward hop of a pair: u_f = U h_f (flip: h_f negated).
+template <typename SF, typename GF, int MU, int S>
+__device__ __forceinline__ HalfSpinor<typename SF::R> hop_fwd(const typename SF::Raw &rs, const typename GF::Raw &ru,
+                                                               bool flip)
+{
+    using R = typename SF::R;
+    HalfSpinor<R> h = project<R, MU, S>(SF::decode(rs));
+    if (flip) negate(h);
+    return su3_mul<R, false>(GF::decode(ru), h);
+}
+
+// The backward hop of a pair, accumulated with the forward result uf.
+template <typename SF, typename GF, int MU, int SFW, int SBW, bool kFirst>
+__device__ __forceinline__ void hop_bwd(Spinor<typename SF::R> &acc, const HalfSpinor<typename SF::R> &uf,
+                                        const typename SF::Raw &rs, const typename GF::Raw &ru, bool flip)
+{
+    using R = typename SF::R;
+    HalfSpinor<R> h = project<R, MU, SBW>(SF::decode(rs));
+    if (flip) negate(h);
+    const HalfSpinor<R> sum = su3_mul_seeded<R, true>(GF::decode(ru), h, uf);
+    accumulate_pair<R, MU, SFW, kFirst>(acc, uf, sum);
 }
 
 // One hop from already fetched raw data: decode, project, multiply,
@@ -247,14 +336,44 @@ __global__ void __launch_bounds__(TPB, (dslash_min_blocks_tpb<SF, GF, TPB>())) d
             ru = ru_n;                                                     \
         }                                                                  \
     }
-        QCD_HOP(0, 0, SF_, false, true)
-        QCD_HOP(1, 0, SB_, true, false)
-        QCD_HOP(2, 1, SF_, false, false)
-        QCD_HOP(3, 1, SB_, true, false)
-        QCD_HOP(4, 2, SF_, false, false)
-        QCD_HOP(5, 2, SB_, true, false)
-        QCD_HOP(6, 3, SF_, false, false)
-        QCD_HOP(7, 3, SB_, true, false)
+        if constexpr (!std::is_same<R, double>::value) {
+            QCD_HOP(0, 0, SF_, false, true)
+            QCD_HOP(1, 0, SB_, true, false)
+            QCD_HOP(2, 1, SF_, false, false)
+            QCD_HOP(3, 1, SB_, true, false)
+            QCD_HOP(4, 2, SF_, false, false)
+            QCD_HOP(5, 2, SB_, true, false)
+            QCD_HOP(6, 3, SF_, false, false)
+            QCD_HOP(7, 3, SB_, true, false)
+        } else {
+            // FP64 (bound by FP64 instructions): the two hops of each
+            // direction as a pair, 48 fewer FP64 instructions per site
+            // (measured 5 % faster at 48^3x12); the 4-byte kernels would need
+            // ~230 registers for it
+            HalfSpinor<R> uf;
+#define QCD_PAIR(K, MU, FIRST)                                                         \
+    {                                                                                  \
+        typename SF::Raw rs_n = SF::fetch(in, nb[K + 1]);                              \
+        typename GF::Raw ru_n = GF::fetch(a.U, lb[K + 1], li[K + 1]);                  \
+        uf = hop_fwd<SF, GF, MU, SF_>(rs, ru, fl[K]);                                  \
+        rs = rs_n;                                                                     \
+        ru = ru_n;                                                                     \
+        if (K + 1 < 7) {                                                               \
+            rs_n = SF::fetch(in, nb[(K + 2) & 7]);                                     \
+            ru_n = GF::fetch(a.U, lb[(K + 2) & 7], li[(K + 2) & 7]);                   \
+        }                                                                              \
+        hop_bwd<SF, GF, MU, SF_, SB_, FIRST>(acc, uf, rs, ru, fl[K + 1]);              \
+        if (K + 1 < 7) {                                                               \
+            rs = rs_n;                                                                 \
+            ru = ru_n;                                                                 \
+        }                                                                              \
+    }
+            QCD_PAIR(0, 0, true)
+            QCD_PAIR(2, 1, false)
+            QCD_PAIR(4, 2, false)
+            QCD_PAIR(6, 3, false)
+#undef QCD_PAIR
+        }
 #undef QCD_HOP
         // epilogue coefficients: kernel parameters, or a device table shared
         // by every launch of a captured CG graph (so one graph serves all
