@@ -471,6 +471,7 @@ cudaError_t hop(const qcd_lattice *lat, const GaugeView &U, int recon, const Hop
     a.state = lat->state;
     a.red_out = lat->red_out;
     a.check_status = h.check_status;
+    a.run_status = h.run_status;
     const bool prof = g_prof_on;
     if (!prof) {
         note_launches();
