@@ -495,8 +495,8 @@ def cpu_oracle_dslash(fields):
 
 
 def cpu_oracle_cg(name="32^3x8"):
-    """One FP64 oracle CG solve of the 32^3x8 twisted-mass even-odd system
-    (configs' C3) on all host cores, to 1e-10."""
+    """One FP64 oracle CG solve of a twisted-mass even-odd workload (32^3x8 or
+    48^3x12) on all host cores, to 1e-10."""
     import oracle
     from paper_1411_5219_gb300 import synthetic as syn
     w = syn.WORKLOADS[name]
@@ -743,6 +743,7 @@ def main():
                                               f"{cb['iters_per_solve']} iterations per solve"}
             line["cpu_baseline"]["dslash"] = cpu_oracle_dslash(host_fields)
             line["cpu_baseline"]["cg_32x8_twisted"] = cpu_oracle_cg()
+            line["cpu_baseline"]["cg_48x12_twisted"] = cpu_oracle_cg("48^3x12")
         except Exception as e:  # the oracle is a baseline, not the product
             line["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
                                     "sample": f"not run: {e}"}

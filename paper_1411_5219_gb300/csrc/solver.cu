@@ -223,6 +223,13 @@ struct CgFields {
     // precision; only an estimate at the target is checked with FP64 Mhat^dag.
     bool split;
     FieldView rhs0;
+    // The precision of the defect's Mhat^dag image: FP32 for 16-bit inner
+    // fields (an FP16 image would carry cond(Mhat) times the FP16 roundoff),
+    // else the inner precision.  With FP32 it is cast to the inner r once.
+    GaugeView Um;
+    int rm_recon;
+    bool mid;               // the image has its own FP32 fields
+    FieldView rho_m, t_m, r_m;
 };
 
 // One CG iteration: q = A p (|Mhat p|^2 -> alpha), x += alpha p, r -= alpha q
@@ -255,8 +262,14 @@ cudaError_t enqueue_true_residual(const CgFields &f, cudaStream_t s)
         check.run_status = CG_VERIFY;
         e = launch_cg_accum_x(f.xh, f.xs, s);
         if (e == cudaSuccess) e = apply_fwd(f.c, f.Uh, f.rh_recon, f.xh, f.sh, f.th, plain_run, s);
-        if (e == cudaSuccess) e = launch_cg_defect(f.rhs0, f.sh, f.rh, f.ss, s);
-        if (e == cudaSuccess) e = apply_dag(f.c, f.Us, f.rs_recon, f.ss, f.rs, f.ts, est, s);
+        if (f.mid) {
+            if (e == cudaSuccess) e = launch_cg_defect(f.rhs0, f.sh, f.rh, f.rho_m, s);
+            if (e == cudaSuccess) e = apply_dag(f.c, f.Um, f.rm_recon, f.rho_m, f.r_m, f.t_m, est, s);
+            if (e == cudaSuccess) e = launch_convert(f.rs, f.r_m, s);
+        } else {
+            if (e == cudaSuccess) e = launch_cg_defect(f.rhs0, f.sh, f.rh, f.ss, s);
+            if (e == cudaSuccess) e = apply_dag(f.c, f.Us, f.rs_recon, f.ss, f.rs, f.ts, est, s);
+        }
         if (e == cudaSuccess) e = apply_dag(f.c, f.Uh, f.rh_recon, f.rh, f.qh, f.th, check, s);
         if (e == cudaSuccess) e = launch_cg_verify(f.qh, f.red, f.state, s);
         if (e == cudaSuccess) e = launch_cg_p(f.ps, f.rs, f.state, s);
@@ -335,8 +348,8 @@ qcd_status cg_graph(const qcd_lattice *lat, const CgFields &f, cudaGraphExec_t *
              f.rs.hv[0].data, f.ps.hv[0].data, f.qs.hv[0].data, f.ts.hv[0].data, f.ss.hv[0].data, f.xs.hv[0].data,
              (void *)f.state, f.rs.prec, f.rhs.nh);
     const size_t used = strlen(key);
-    snprintf(key + used, sizeof(key) - used, "|%p|%d|%d|%p", (void *)f.red.partials, f.rs.rhs_log2, (int)f.split,
-             f.rhs0.hv[0].data);
+    snprintf(key + used, sizeof(key) - used, "|%p|%d|%d|%p|%d|%p|%p", (void *)f.red.partials, f.rs.rhs_log2,
+             (int)f.split, f.rhs0.hv[0].data, (int)f.mid, f.Um.data, f.r_m.hv[0].data);
     auto it = lat->graphs.find(key);
     if (it != lat->graphs.end()) {
         it->second.last_use = ++lat->graph_clock;
@@ -619,8 +632,19 @@ qcd_status qcd::solve_impl(const qcd_gauge *g, qcd_spinor *const *x, const qcd_s
 
     // ---- CG
     const bool split = mixed && (c.eo || !prm->normal);
+    const bool mid = split && (sp == QCD_PREC_F16 || sp == QCD_PREC_BF16);
+    GaugeView Um = Us;
+    FieldView rho_m{}, t_m{}, r_m{};
+    if (mid) {
+        Um = gauge_view(g, QCD_PREC_F32, srecon, s, &st);
+        if (st != QCD_OK) return st;
+        rho_m = ws_field(lat, "cg_rho32", nh, QCD_PREC_F32, L);
+        t_m = ws_field(lat, "cg_t32", 1, QCD_PREC_F32, L);
+        r_m = ws_field(lat, "cg_r32", nh, QCD_PREC_F32, L);
+        if (!rho_m.hv[0].data || !t_m.hv[0].data || !r_m.hv[0].data) return fail(QCD_ERR_OOM, "solve_cg: workspace");
+    }
     CgFields F{c, Uh, Us, g->recon, srecon, mixed, rhs, xh, rh, qh, th, sh, rs, ps, qs, ts, ss, xs, red, lat->state,
-               split, c.eo ? bp : bf};
+               split, c.eo ? bp : bf, Um, srecon, mid, rho_m, t_m, r_m};
     const double delta = mixed ? prm->reliable_delta : 0.0;
     RhsValues tol2{};
     for (int k = 0; k < kMaxRhs; ++k) tol2.v[k] = prm[k < nrhs ? k : 0].tol * prm[k < nrhs ? k : 0].tol;
@@ -643,7 +667,7 @@ qcd_status qcd::solve_impl(const qcd_gauge *g, qcd_spinor *const *x, const qcd_s
         // kernels the graph ran: per trip the iteration and two control
         // kernels, per reliable update its body
         const int op = c.eo ? 4 : 2;
-        const int per_update = split ? (c.eo ? 10 : 7) : op + 2 + (mixed ? 1 : 0);
+        const int per_update = split ? (c.eo ? 10 : 7) + (mid ? 1 : 0) : op + 2 + (mixed ? 1 : 0);
         note_launches(lat->state_host->trips * (op + 4) + lat->state_host->reliable_updates * per_update);
     } else {
         QCD_TRY(cg_eager(lat, F, s), "solve_cg: iterations");

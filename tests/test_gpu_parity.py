@@ -269,6 +269,22 @@ def test_solve_eo_matches_oracle(q, inner, kappa, mu):
         assert st["reliable_updates"] >= 1
 
 
+@pytest.mark.parametrize("inner", ["f16", "bf16", "f32"])
+@pytest.mark.parametrize("kappa", [0.12, 0.125, 0.13])
+def test_solve_mixed_near_critical_kappa(q, inner, kappa):
+    """Near the critical kappa of these near-identity links the Schur operator
+    is badly conditioned: the mixed solve must still reach the FP64 target
+    (the defect's Mhat^dag image is formed in FP32, not in 16 bits)."""
+    dims = (8, 8, 8, 4)
+    lat, U, g = gauge(q, dims, eps=0.2, seed=1107)
+    src = syn.gaussian_spinor(dims, 86)
+    b, x = q.Spinor(lat, "full", "f64"), q.Spinor(lat, "full", "f64")
+    b.upload(src)
+    status, st = q.solve_cg(g, x, b, kappa, 0.0, tol=1e-10, inner_prec=inner)
+    assert status == 0 and st["true_rel_residual"] <= 1e-10, st
+    assert schur_residual_oracle(U, src, x.download(), kappa, 0.0) <= 1.5e-10
+
+
 def test_solve_full_cgnr_matches_eo(q):
     dims = (4, 4, 4, 8)
     lat, U, g = gauge(q, dims, eps=0.2, seed=90)
@@ -328,6 +344,31 @@ def test_dslash_full_size_sampled(q, name):
     assert np.all(np.isfinite(out))
 
 
+@pytest.mark.parametrize("name", ["24^3x8", "48^3x12"])
+@pytest.mark.parametrize("prec,recon", [("f32", 12), ("f16", 12), ("bf16", 12), ("f16", 8)])
+def test_dslash_low_precision_full_size_sampled(q, name, prec, recon):
+    """The inner-solver formats at the benchmark volumes, in the bench's launch
+    shape: 4096 sampled output sites against the oracle, norm-wise within the
+    storage tolerance, and every output finite."""
+    w = syn.WORKLOADS[name]
+    dims = w["dims"]
+    lat, U, g = gauge(q, dims, recon=recon, eps=w["eps"], seed=w["seed"])
+    psi = syn.gaussian_spinor(dims, w["seed"] + 7)
+    half_in = syn.to_half(psi, 1)
+    si, so = q.Spinor(lat, "odd", prec), q.Spinor(lat, "even", prec)
+    si.upload(half_in)
+    q.apply_dslash(g, so, si)
+    out = so.download()
+    full_in = psi * (syn.parity_of_sites(dims) == 1)[..., None, None]
+    even_sites = np.flatnonzero(syn.parity_of_sites(dims).reshape(-1) == 0)
+    rng = np.random.default_rng(1)
+    pick = np.sort(rng.choice(len(even_sites), 4096, replace=False))
+    pick[:2] = [0, len(even_sites) - 1]
+    want = oracle.dhop_sites(U, full_in, even_sites[pick])
+    assert F.rel_err(out[pick], want) <= tol_of(prec), (name, prec, recon)
+    assert np.all(np.isfinite(out))
+
+
 def test_solve_48x12_twisted_full_size(q):
     """The 48^3 x 12 twisted-mass workload (kappa 0.16, mu 0.01) at full size,
     as the bench runs it: the FP16 mixed solve and the FP64 solve both reach
@@ -347,6 +388,11 @@ def test_solve_48x12_twisted_full_size(q):
         xs[inner] = x.download()
     assert schur_residual_oracle(U, b, xs["f16"], kappa, mu) <= 1.5e-10
     assert F.rel_err(xs["f16"], xs["f64"]) <= 1e-8
+    # the oracle's own even-odd CG at this volume, run once to 1e-12
+    xo, sto = oracle.solve_eo(U, b, kappa, mu, tol=1e-12)
+    assert sto[1] <= 1e-12
+    for inner in ("f16", "f64"):
+        assert F.rel_err(xs[inner], xo) <= 1e-8, inner
 
 
 def test_solve_eo_24x8_true_residual(q):
