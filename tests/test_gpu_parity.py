@@ -300,6 +300,27 @@ def test_solve_full_cgnr_matches_eo(q):
     assert F.rel_err(xs[0], xs[1]) <= 1e-8
 
 
+@pytest.mark.parametrize("inner", ["f16", "f32"])
+@pytest.mark.parametrize("normal", [False, True])
+def test_solve_full_lattice_mixed(q, inner, normal):
+    """Mixed-precision CG on the full lattice: CGNR on M (its reliable update
+    uses the FP64 defect b - M x) and CG on M^dag M x = b (four-hop FP64
+    recomputation), against the oracle's solves."""
+    dims = (4, 4, 4, 8)
+    kappa, mu = 0.15, 0.02
+    lat, U, g = gauge(q, dims, eps=0.2, seed=90)
+    b = syn.gaussian_spinor(dims, 92)
+    bs, x = q.Spinor(lat, "full", "f64"), q.Spinor(lat, "full", "f64")
+    bs.upload(b)
+    status, st = q.solve_cg(g, x, bs, kappa, mu, tol=1e-10, eo=False, normal=normal, inner_prec=inner)
+    assert status == 0 and st["true_rel_residual"] <= 1e-10, st
+    if normal:
+        xo, _ = oracle.solve_mdagm(U, b, kappa, mu, tol=1e-12)
+    else:
+        xo, _ = oracle.solve_m(U, b, kappa, mu, tol=1e-12)
+    assert F.rel_err(x.download(), xo) <= 1e-7
+
+
 def test_solve_zero_source_and_errors(q):
     dims = (4, 4, 4, 4)
     lat, U, g = gauge(q, dims)
