@@ -415,6 +415,13 @@ def serving_block(qcd, torch, n_requests=2000, rate=30.0, slots=8, seed=1006):
            "service_ms_median_by_volume": {k: float(np.median(v) * 1e3) for k, v in per_vol.items()},
            "all_ok": all(r["status"] == 0 for r in results),
            "max_true_rel_residual": max(r["stats"]["true_rel_residual"] for r in results)}
+    bad = [{"volume": "x".join(map(str, vols[vi])), "field": gk, "kappa": round(kappa, 5), "status": r["status"],
+            "slot": r["slot"], "iterations": r["stats"]["iterations"],
+            "true_rel_residual": r["stats"]["true_rel_residual"]}
+           for (vi, gk, kappa), r in zip(picks, results) if r["status"] != 0]
+    out["failed"] = len(bad)
+    if bad:
+        out["failures"] = bad[:10]
     sv.close()
     return out
 

@@ -126,10 +126,11 @@ qcd_status qcd_gauge_create(const qcd_lattice *lat, qcd_prec prec, qcd_recon rec
  * reach, see qcd_recon); CUDA. */
 qcd_status qcd_gauge_upload(qcd_gauge *g, const double *host, void *stream);
 /* Build (if missing) the derived copy used by kernels of precision
- * `prec` with `recon` reals per link.  Optional: kernels build it on first
- * use (a recon-8 copy must be built outside stream capture, since its
- * check reads back to the host).  Errors: INVALID_ARG (also recon-8 links
- * out of reach); OOM. */
+ * `prec` with `recon` reals per link.  Optional: calls build it on first
+ * use, outside stream capture (a new copy is complete, its stream
+ * synchronised, before any stream may read it; a call on a capturing stream
+ * that needs a missing copy fails with INVALID_ARG).  Errors: INVALID_ARG
+ * (also recon-8 links out of reach); OOM. */
 qcd_status qcd_gauge_prepare(qcd_gauge *g, qcd_prec prec, qcd_recon recon, void *stream);
 void qcd_gauge_destroy(qcd_gauge *g);
 

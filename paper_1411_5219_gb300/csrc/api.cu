@@ -229,6 +229,16 @@ FieldView ws_field(const qcd_lattice *lat, const std::string &name, int nh, int 
 
 Reduction reduction_of(const qcd_lattice *lat) { return Reduction{lat->red_partials, lat->red_counter, lat->red_cap}; }
 
+// Zero a new device buffer before any stream may use it.  A plain memset
+// runs on the legacy default stream, which non-blocking streams (a server
+// slot's, a user's) do not wait for: finished here, it cannot land after
+// the first kernels that read or fill the buffer.
+cudaError_t zero_now(void *p, size_t n)
+{
+    cudaError_t e = cudaMemsetAsync(p, 0, n, cudaStreamLegacy);
+    return e == cudaSuccess ? cudaStreamSynchronize(cudaStreamLegacy) : e;
+}
+
 GaugeView gauge_view(const qcd_gauge *g, int prec, int recon, cudaStream_t s, qcd_status *st)
 {
     *st = QCD_OK;
@@ -240,6 +250,16 @@ GaugeView gauge_view(const qcd_gauge *g, int prec, int recon, cudaStream_t s, qc
     std::lock_guard<std::mutex> lk(derived_mu);
     auto it = gm->derived.find(key);
     if (it != gm->derived.end()) return GaugeView{it->second.first, stride};
+    // The copy is converted on `s` and then published to every stream, so
+    // the conversion must be complete first: it is built outside stream
+    // capture and the stream is synchronised before the pointer is stored.
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        *st = fail(QCD_ERR_INVALID_ARG, "gauge copy: a copy in a new precision is built outside stream capture "
+                                        "(call qcd_gauge_prepare first)");
+        return GaugeView{nullptr, stride};
+    }
     const size_t bytes = gauge_bytes(prec, recon, stride);
     void *p = nullptr;
     DeviceLock dl(device_mutex());
@@ -261,6 +281,12 @@ GaugeView gauge_view(const qcd_gauge *g, int prec, int recon, cudaStream_t s, qc
             cudaFree(p);
             return GaugeView{nullptr, stride};
         }
+    }
+    e = cudaStreamSynchronize(s);  // other streams may use the copy as soon as it is stored
+    if (e != cudaSuccess) {
+        cudaFree(p);
+        *st = check_cuda(e, "gauge copy");
+        return GaugeView{nullptr, stride};
     }
     gm->derived[key] = {p, bytes};
     return dst;
@@ -471,7 +497,6 @@ cudaError_t hop(const qcd_lattice *lat, const GaugeView &U, int recon, const Hop
     a.state = lat->state;
     a.red_out = lat->red_out;
     a.check_status = h.check_status;
-    a.run_status = h.run_status;
     const bool prof = g_prof_on;
     if (!prof) {
         note_launches();
@@ -606,8 +631,8 @@ qcd_status qcd_lattice_create(const int dims[4], int t_bc, qcd_lattice **out)
     if (e == cudaSuccess) e = cudaMalloc(&lat->state, sizeof(CgState));
     if (e == cudaSuccess) e = cudaMallocHost(&lat->state_host, sizeof(CgState));
     if (e == cudaSuccess) e = cudaMallocHost(&lat->coef_host, kCoefHostDoubles * sizeof(double));
-    if (e == cudaSuccess) e = cudaMemset(lat->red_counter, 0, 64);
-    if (e == cudaSuccess) e = cudaMemset(lat->state, 0, sizeof(CgState));
+    if (e == cudaSuccess) e = zero_now(lat->red_counter, 64);
+    if (e == cudaSuccess) e = zero_now(lat->state, sizeof(CgState));
     if (e != cudaSuccess) {
         qcd_status st = check_cuda(e, "lattice_create");
         dl.unlock();
@@ -656,7 +681,12 @@ qcd_status qcd_gauge_create(const qcd_lattice *lat, qcd_prec prec, qcd_recon rec
         delete g;
         return fail(QCD_ERR_OOM, "gauge_create: cudaMalloc(%zu) failed", gauge_bytes(prec, recon, lat->stride));
     }
-    cudaMemset(g->data, 0, g->bytes);
+    if (zero_now(g->data, g->bytes) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(g->data);
+        delete g;
+        return fail(QCD_ERR_CUDA, "gauge_create: zeroing the field failed");
+    }
     *out = g;
     return QCD_OK;
 }
@@ -747,8 +777,8 @@ qcd_status qcd_spinor_create(const qcd_lattice *lat, qcd_parity parity, qcd_prec
     DeviceLock dl(device_mutex());
     cudaError_t e = cudaMalloc(&s->data, nh * s->half_data_bytes);
     if (e == cudaSuccess && s->half_norm_bytes) e = cudaMalloc(reinterpret_cast<void **>(&s->norm), nh * s->half_norm_bytes);
-    if (e == cudaSuccess) e = cudaMemset(s->data, 0, nh * s->half_data_bytes);
-    if (e == cudaSuccess && s->norm) e = cudaMemset(s->norm, 0, nh * s->half_norm_bytes);
+    if (e == cudaSuccess) e = zero_now(s->data, nh * s->half_data_bytes);
+    if (e == cudaSuccess && s->norm) e = zero_now(s->norm, nh * s->half_norm_bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         cudaFree(s->data);
@@ -779,8 +809,8 @@ qcd_status qcd_spinor_create_ks(const qcd_lattice *lat, qcd_parity parity, qcd_p
     DeviceLock dl(device_mutex());
     cudaError_t e = cudaMalloc(&s->data, nh * s->half_data_bytes);
     if (e == cudaSuccess && s->half_norm_bytes) e = cudaMalloc(reinterpret_cast<void **>(&s->norm), nh * s->half_norm_bytes);
-    if (e == cudaSuccess) e = cudaMemset(s->data, 0, nh * s->half_data_bytes);
-    if (e == cudaSuccess && s->norm) e = cudaMemset(s->norm, 0, nh * s->half_norm_bytes);
+    if (e == cudaSuccess) e = zero_now(s->data, nh * s->half_data_bytes);
+    if (e == cudaSuccess && s->norm) e = zero_now(s->norm, nh * s->half_norm_bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         cudaFree(s->data);

@@ -273,7 +273,7 @@ template <typename SF, typename GF, int kDagger, int kEpi, bool kReduce, int TPB
 __global__ void __launch_bounds__(TPB, (dslash_min_blocks_tpb<SF, GF, TPB>())) dslash_kernel(const DslashLaunch a)
 {
     using R = typename SF::R;
-    if (a.check_status && a.state->status != a.run_status) return;
+    if (a.check_status && a.state->status != CG_RUNNING) return;
     constexpr int SF_ = kDagger ? -1 : +1;  // projector sign of forward hops
     constexpr int SB_ = -SF_;                // ... of backward hops
     // element e = site i * 2^rhs_log2 + rhs (one rhs: e = i)

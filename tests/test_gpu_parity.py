@@ -273,8 +273,8 @@ def test_solve_eo_matches_oracle(q, inner, kappa, mu):
 @pytest.mark.parametrize("kappa", [0.12, 0.125, 0.13])
 def test_solve_mixed_near_critical_kappa(q, inner, kappa):
     """Near the critical kappa of these near-identity links the Schur operator
-    is badly conditioned: the mixed solve must still reach the FP64 target
-    (the defect's Mhat^dag image is formed in FP32, not in 16 bits)."""
+    is badly conditioned: the mixed solve, whose reliable updates recompute
+    the residual in FP64, must still reach the FP64 target."""
     dims = (8, 8, 8, 4)
     lat, U, g = gauge(q, dims, eps=0.2, seed=1107)
     src = syn.gaussian_spinor(dims, 86)
@@ -303,9 +303,9 @@ def test_solve_full_cgnr_matches_eo(q):
 @pytest.mark.parametrize("inner", ["f16", "f32"])
 @pytest.mark.parametrize("normal", [False, True])
 def test_solve_full_lattice_mixed(q, inner, normal):
-    """Mixed-precision CG on the full lattice: CGNR on M (its reliable update
-    uses the FP64 defect b - M x) and CG on M^dag M x = b (four-hop FP64
-    recomputation), against the oracle's solves."""
+    """Mixed-precision CG on the full lattice, CGNR on M and CG on
+    M^dag M x = b (each reliable update recomputes the residual in FP64),
+    against the oracle's solves."""
     dims = (4, 4, 4, 8)
     kappa, mu = 0.15, 0.02
     lat, U, g = gauge(q, dims, eps=0.2, seed=90)
@@ -729,6 +729,57 @@ def test_server_same_alone_and_in_mix(q):
     sv.close()
 
 
+def test_server_concurrent_first_use_of_a_precision(q):
+    """Requests on a gauge field with no prepared copies, running at the same
+    time on several slots: the copies they need (FP16 links, FP32 links for
+    the reliable updates) are built by whichever solve comes first, and no
+    other slot may read one before its conversion is complete."""
+    dims = (16, 16, 16, 8)
+    lat = q.Lattice(dims, -1)
+    U = syn.gauge_field(dims, 0.2, 312)
+    g = q.Gauge(lat, "f64", 18)
+    g.upload(U)
+    sv = q.Server(slots=4, memory_budget=8 << 30)
+    gid = sv.add_gauge(g)
+    jobs = []
+    for k in range(8):
+        b = syn.gaussian_spinor(dims, 600 + k)
+        x = np.empty_like(b)
+        jobs.append((sv.submit(gid, b, x, 0.13 + 0.004 * k, inner_prec="f16"), b, x, 0.13 + 0.004 * k))
+    for rid, b, x, kappa in jobs:
+        r = sv.wait(rid)
+        assert r["status"] == 0 and r["stats"]["true_rel_residual"] <= 1e-10, r
+    for rid, b, x, kappa in jobs[:2]:
+        assert schur_residual_oracle(U, b, x, kappa, 0.0) <= 1.5e-10
+    sv.close()
+
+
+def test_created_fields_are_zeroed_before_other_streams_use_them(q):
+    """A new lattice (CG state, reduction counter), gauge field and spinor are
+    zeroed before their create call returns.  With the legacy default stream
+    held busy by a bounded spin kernel, fields created next and filled on a
+    non-blocking stream keep what was uploaded, and a solve on that stream
+    over a fresh lattice converges."""
+    import torch
+    dims = (8, 8, 8, 4)
+    U = syn.gauge_field(dims, 0.2, 1401)
+    src = syn.gaussian_spinor(dims, 1402)
+    side = torch.cuda.Stream()  # created non-blocking: no implicit wait on the legacy stream
+    torch.cuda.synchronize()
+    with torch.cuda.stream(torch.cuda.default_stream()):
+        torch.cuda._sleep(200_000_000)  # ~0.1 s on the legacy default stream
+    lat = q.Lattice(dims)
+    g = q.Gauge(lat)
+    g.upload(U, stream=side)
+    b, x = q.Spinor(lat, "full", "f64"), q.Spinor(lat, "full", "f64")
+    b.upload(src, stream=side)
+    status, st = q.solve_cg(g, x, b, 0.15, 0.0, tol=1e-10, inner_prec="f16", stream=side)
+    torch.cuda.synchronize()
+    assert status == 0 and st["true_rel_residual"] <= 1e-10, st
+    assert np.array_equal(b.download(), src)
+    assert schur_residual_oracle(U, src, x.download(), 0.15, 0.0) <= 1.5e-10
+
+
 def test_server_overlap_and_memory_budget(q):
     lat, U, g = _server_problem(q, (8, 8, 8, 4), 310)
     lat2, U2, g2 = _server_problem(q, (16, 16, 16, 8), 311)
@@ -745,10 +796,24 @@ def test_server_overlap_and_memory_budget(q):
     res = [sv.wait(i) for i, _ in jobs]
     assert all(r["status"] == 0 for r in res)
     assert sv.info()["used_bytes"] <= one_ctx + 24 * 2 * (8 ** 3 * 4 // 2) * 192
-    # concurrency: some requests ran at the same time on different slots
-    iv = sorted((r["t_start"], r["t_end"], r["slot"]) for r in res)
+    # concurrency, with room for every slot's context (under the tight budget
+    # above most requests first rebuild an evicted context, so whether two
+    # happen to overlap depends on timing): requests run at the same time
+    # on different slots
+    roomy = q.Server(slots=4, memory_budget=8 << 30)
+    rg, rg2 = roomy.add_gauge(g), roomy.add_gauge(g2)
+    rjobs = []
+    for k in range(16):
+        gg, d = (rg, (8, 8, 8, 4)) if k % 2 == 0 else (rg2, (16, 16, 16, 8))
+        b = syn.gaussian_spinor(d, 520 + k)
+        x = np.empty_like(b)
+        rjobs.append(roomy.submit(gg, b, x, 0.13, inner_prec="f16"))
+    rres = [roomy.wait(i) for i in rjobs]
+    assert all(r["status"] == 0 for r in rres)
+    iv = sorted((r["t_start"], r["t_end"], r["slot"]) for r in rres)
     overlaps = sum(1 for a, b_ in zip(iv, iv[1:]) if b_[0] < a[1] and b_[2] != a[2])
     assert overlaps >= 1
+    roomy.close()
     big = q.Server(slots=1, memory_budget=1 << 20)
     gbig = big.add_gauge(g2)
     b = syn.gaussian_spinor((16, 16, 16, 8), 1)
