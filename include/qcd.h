@@ -107,8 +107,10 @@ qcd_status qcd_stream_sync(void *stream);
  * be even and >= 2 (even-odd indexing needs even Lx; the boundary factor
  * needs even extents for a consistent parity).  t_bc = +1 (periodic) or -1
  * (antiperiodic) in time (Sec. 1 discretises space-time on an Ns^3 x Nt
- * hypercube).  Errors: INVALID_ARG for bad extents or a volume too large
- * for 32-bit site indices; OOM. */
+ * hypercube).  Its device state (CG state, reduction counters) is zeroed
+ * before the call returns, so any stream may use the lattice at once; the
+ * call waits for the legacy default stream.  Errors: INVALID_ARG for bad
+ * extents or a volume too large for 32-bit site indices; OOM. */
 qcd_status qcd_lattice_create(const int dims[4], int t_bc, qcd_lattice **out);
 void qcd_lattice_destroy(qcd_lattice *lat);
 
@@ -118,7 +120,9 @@ void qcd_lattice_destroy(qcd_lattice *lat);
  * on the device per (parity, mu) block, site-fastest (SoA, Sec. 4), in
  * precision `prec` and with `recon` reals per link.  The field also keeps
  * derived copies in other precisions, made on the device from this one on
- * first use by a Dslash of that precision.  Errors: INVALID_ARG; OOM. */
+ * first use by a Dslash of that precision.  The field is zero when the
+ * call returns (it waits for the legacy default stream).  Errors:
+ * INVALID_ARG; OOM; CUDA. */
 qcd_status qcd_gauge_create(const qcd_lattice *lat, qcd_prec prec, qcd_recon recon, qcd_gauge **out);
 /* Copy a host gauge field (host layout above, 4*V*9 complex doubles) to
  * the device and convert it; drops derived copies.  Recon-12 and recon-8
@@ -138,7 +142,10 @@ void qcd_gauge_destroy(qcd_gauge *g);
 
 /* A spinor (fermion) field, 4 spins x 3 colours per site (Sec. 4), on one
  * parity (EVEN/ODD, V/2 sites) or on all sites (FULL = even half then odd
- * half).  F16 keeps one FP32 scale per site.  Errors: INVALID_ARG; OOM. */
+ * half).  F16 keeps one FP32 scale per site.  The field is zero when the
+ * call returns, so an upload on any stream, blocking or not, is not
+ * overwritten later (the call waits for the legacy default stream).
+ * Errors: INVALID_ARG; OOM. */
 qcd_status qcd_spinor_create(const qcd_lattice *lat, qcd_parity parity, qcd_prec prec, qcd_spinor **out);
 /* A staggered field (one colour vector, 3 complex per site), the field of
  * the paper's second Dirac operator D_KS (Sec. 1, Sec. 6), in F64, F32, F16
