@@ -312,3 +312,28 @@ def test_synthetic_links_are_su3_and_deterministic():
     assert np.abs(np.linalg.det(u) - 1).max() < 1e-14
     # near-unit: |U - 1| of order eps
     assert 0.05 < np.abs(u - np.eye(3)).mean() < 0.3
+
+
+def test_splitmix64_matches_its_published_sequence():
+    """The generator behind every synthetic input is SplitMix64 (Steele, Lea
+    and Flood, OOPSLA 2014).  Started from state 0, the reference generator
+    (state += 0x9E3779B97F4A7C15, then the output mix) yields this sequence."""
+    gamma = np.uint64(0x9E3779B97F4A7C15)
+    with np.errstate(over="ignore"):
+        states = np.array([0, gamma, np.uint64(2) * gamma], dtype=np.uint64)
+    got = [int(v) for v in syn._splitmix64(states)]
+    assert got == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_uniform_and_normal_draws():
+    """Uniforms lie in the open interval (0, 1); the Box-Muller normals have
+    mean 0 and variance 1 within their sampling error, and any slice of the
+    sequence is drawn on its own."""
+    u = syn.uniform(7, syn.STREAM_AUX, np.arange(1 << 16, dtype=np.uint64))
+    assert u.min() > 0.0 and u.max() < 1.0
+    assert abs(u.mean() - 0.5) < 5 * np.sqrt(1 / 12 / u.size)
+    z = syn.normal(7, syn.STREAM_AUX, 0, 1 << 18)
+    assert abs(z.mean()) < 5 / np.sqrt(z.size)
+    assert abs(z.var() - 1.0) < 5 * np.sqrt(2 / z.size)
+    assert abs((z ** 4).mean() - 3.0) < 0.1  # Gaussian fourth moment
+    assert np.array_equal(syn.normal(7, syn.STREAM_AUX, 1000, 24), z[1000:1024])
