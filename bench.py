@@ -117,23 +117,32 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.f.close()
-        rows = []
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 8:
-                continue
-            try:
-                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
-            except ValueError:
-                continue
-        if not rows:
-            return None
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
-        sm = [r[0] for r in rows]
-        loaded = [v for v in sm if v >= 0.5 * max(sm)] or sm
-        return {"sm_mhz": float(np.median(loaded)), "sm_max_mhz": float(max(r[1] for r in rows)),
-                "reasons": reasons, "samples": len(rows)}
+        with open(self.path) as f:
+            return summarize_clocks(f)
+
+
+def summarize_clocks(lines):
+    """Summary of nvidia-smi rows in ClockSampler.FIELDS order (csv, no
+    header, no units): median SM clock over the loaded samples (those at
+    half the peak seen or more), the maximum SM clock, the throttle reasons
+    seen active, and the sample count.  None when no row parses."""
+    rows = []
+    for line in lines:
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) < 8:
+            continue
+        try:
+            rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+        except ValueError:
+            continue
+    if not rows:
+        return None
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+    sm = [r[0] for r in rows]
+    loaded = [v for v in sm if v >= 0.5 * max(sm)] or sm
+    return {"sm_mhz": float(np.median(loaded)), "sm_max_mhz": float(max(r[1] for r in rows)),
+            "reasons": reasons, "samples": len(rows)}
 
 
 # ------------------------------------------------------------------ problem

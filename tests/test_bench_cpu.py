@@ -1,6 +1,7 @@
 """Host-side logic of bench.py that needs no GPU: the max-over-ranks timing
-of the multi-process run (world size 2 on the gloo backend) and the CPU
-oracle reference arm (rank 0 prints the JSON line, other ranks do no work)."""
+of the multi-process run (world size 2 on the gloo backend), the CPU
+oracle reference arm (rank 0 prints the JSON line, other ranks do no work)
+and the summary of the clock samples taken during the timed region."""
 
 import json
 import os
@@ -73,3 +74,19 @@ def test_reference_arm_prints_contract_line():
         assert k in line
     assert line["impl"] == "reference" and line["unit"] == "solves/s" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_clock_summary_of_nvidia_smi_rows():
+    sys.path.insert(0, ROOT)
+    import bench
+    idle = "345, 2070, 150.1, 0x0000000000000001, Not Active, Not Active, Not Active, Not Active"
+    busy = "2070, 2070, 900.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active"
+    capped = "1980, 2070, 1400.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active"
+    rows = [idle, busy, busy, capped, busy, "garbage line", "[N/A], 2070, 1, 0, a, b, c, d", ""]
+    out = bench.summarize_clocks(rows)
+    # the idle sample (below half the peak) is left out of the median
+    assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 5}
+    hot = "1500, 2070, 1200.0, 0x0000000000000048, Active, Active, Not Active, Not Active"
+    out = bench.summarize_clocks([busy, hot, hot])
+    assert out["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"] and out["sm_mhz"] == 1500.0
+    assert bench.summarize_clocks(["", "x, y"]) is None
