@@ -208,6 +208,8 @@ FieldView view_of(const qcd_spinor *s)
 
 FieldView ws_field(const qcd_lattice *lat, const std::string &name, int nh, int prec, int rhs_log2)
 {
+    // fits an int: lattice creation demands h * Lmax < 2^32 with Lmax >=
+    // (2h)^(1/4), so h < 2^25.4 and h * kMaxRhs * 2 parities < 2^30.4
     const int ne = lat->h << rhs_log2;
     const int stride = rhs_log2 == 0 ? lat->stride : (ne + 63) / 64 * 64;
     const size_t db = spinor_half_bytes(prec, stride), nb = spinor_half_norm_bytes(prec, stride);
