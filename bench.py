@@ -29,6 +29,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -88,7 +89,7 @@ class ClockSampler:
 
     def __init__(self, device_index: int):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"qcd_bench_clocks_{os.getpid()}_{device_index}.csv")
         self.dev = str(device_index)
         try:
             import torch
@@ -254,7 +255,7 @@ def dslash_sweep(qcd, torch, flush, hbm, reps=20, fields=None):
 
 
 def batched_block(qcd, torch, flush, hbm, reps):
-    """configs[3]: 32^3x8 even-odd Wilson, 12 point + 4 Gaussian sources, FP32
+    """Batched solves: 32^3x8 even-odd Wilson, 12 point + 4 Gaussian sources, FP32
     inner / FP64 reliable updates: one batched CG against 16 single solves,
     and the 16-rhs Dslash against the single-rhs one."""
     from paper_1411_5219_gb300 import synthetic as syn
@@ -356,7 +357,7 @@ def batched_block(qcd, torch, flush, hbm, reps):
 
 
 def serving_block(qcd, torch, n_requests=2000, rate=30.0, slots=8, seed=1006):
-    """configs[4]: a Poisson stream of even-odd solves of five volumes, kappa
+    """Serving: a Poisson stream of even-odd solves of five volumes, kappa
     uniform in [0.12, 0.16], 3 resident gauge fields per volume, FP16-mixed
     CG to 1e-10, admitted by slot and device-memory budget."""
     import threading
