@@ -44,9 +44,19 @@ TOL = 1e-10
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x FP64 FMA/clk x 2 flop x max clock
 HBM_FALLBACK_GBS = 6800.0
 # DRAM bytes (read + write) of one FP64 D_eo launch at 24^3 x 8 from an ncu
-# capture of the current kernel (profiles/dslash_f64_r18_24x24x24x8.md);
+# capture of the current kernel;
 # set to None when the kernel changes.
 TRAFFIC_F64_D_24 = 76.38e6
+
+
+def workload_config():
+    """The `config` of both arms' JSON lines (the same keys and values)."""
+    from paper_1411_5219_gb300 import synthetic as syn
+    w = syn.WORKLOADS[WORKLOAD]
+    return {"workload": "24^3x8 even-odd Wilson kappa=0.155, eps=0.2 links, Gaussian source, FP64 CG to 1e-10",
+            "lattice": list(w["dims"]), "kappa": w["kappa"], "tol": TOL,
+            "parallelism": "replicas: one independent solve per rank (the CPU oracle arm runs on rank 0 only)",
+            "l2": "GPU arm: L2 flushed before every timed solve (512 MiB write); CPU oracle arm: no flush"}
 
 
 def peaks():
@@ -526,6 +536,42 @@ def cpu_oracle_cg(name="32^3x8"):
             "cores": oracle.get_threads()}
 
 
+def _sig(v, n=4):
+    """v rounded to n significant digits (None stays None)."""
+    if v is None:
+        return None
+    return float(f"{v:.{n}g}")
+
+
+def mixed_summary(mixed):
+    """Solves/s of the FP16-mixed and the FP64 CG per workload, their ratio and
+    the worst true residual (both solvers to 1e-10)."""
+    out = {}
+    for name, m in mixed.items():
+        res = max(m.get("mixed_true_rel_residual", 0.0), m.get("fp64_true_rel_residual", 0.0))
+        out[name.split(" ")[0] + (" tm" if "twisted" in name else "")] = {
+            "fp64": _sig(m["fp64_solves_s"]), "f16_mixed": _sig(m["mixed_f16_solves_s"]), "ratio": _sig(m["ratio"], 3),
+            "max_res": _sig(res, 2)}
+    return out
+
+
+def serving_summary(sv):
+    return {"requests": sv["requests"], "rate_per_s": sv["arrival_rate_per_s"], "solves_s": _sig(sv["solves_s"]),
+            "p50_ms": _sig(sv["latency_p50_ms"], 3), "p99_ms": _sig(sv["latency_p99_ms"], 3),
+            "failed": sv["failed"], "max_res": _sig(sv["max_true_rel_residual"], 2)}
+
+
+def batched_summary(b):
+    out = {"sources_16_speedup": _sig(b["solve"]["speedup"], 3),
+           "sources_16_solves_s": _sig(b["solve"]["batched_solves_s"]),
+           "kappa_16_speedup": _sig(b["kappa_batch"]["speedup"], 3),
+           "max_res": _sig(max(b["solve"]["max_true_rel_residual"], b["kappa_batch"]["max_true_rel_residual"]), 2)}
+    for k in ("dslash_f32_r12", "dslash_f16_r12"):
+        if k in b:
+            out[k + "_rhs_speedup"] = _sig(b[k]["rhs_per_s_16rhs"] / b[k]["rhs_per_s_1rhs"], 3)
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -551,9 +597,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(ts)) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "24^3x8 even-odd Wilson kappa=0.155, eps=0.2 links, Gaussian source, "
-                                   "FP64 CG to 1e-10", "lattice": list(w["dims"]), "kappa": w["kappa"],
-                       "tol": TOL},
+            "config": workload_config(),
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": oracle.get_threads(), "kind": "oracle",
                              "sample": f"each step = {n_it} FP64 oracle CG iterations of the 24^3x8 even-odd "
                                        f"system, scaled by the oracle's {iters} iterations per solve"},
@@ -666,10 +710,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "24^3x8 even-odd Wilson kappa=0.155, eps=0.2 links, Gaussian source, "
-                               "FP64 CG to 1e-10",
-                   "lattice": list(prob.dims), "kappa": prob.kappa, "tol": TOL, "parallelism": "replicas",
-                   "l2": "flushed before every timed solve (512 MiB write)"},
+        "config": workload_config(),
         "iterations": int(np.median(iters)), "true_rel_residual": resid,
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu", "kernel": "dslash FP64 (D_eo/D_oe with fused epilogues) in the CG",
@@ -715,6 +756,7 @@ def main():
             "ratio": (args.steps / float(np.sum(tm))) / value,
             "fp64_iters": int(np.median(iters)), "mixed_iters": sm["iterations"],
             "reliable_updates": sm["reliable_updates"], "mixed_true_rel_residual": sm["true_rel_residual"],
+            "fp64_true_rel_residual": resid,
             "mixed_rel_err_vs_fp64_x": float(np.linalg.norm(xm - x64) / np.linalg.norm(x64)),
             "f16_dslash_GB_s": f16d["bytes"] / (f16d["ms"] * 1e-3) / 1e9 if f16d["ms"] else None,
             "f16_dslash_frac_hbm": (f16d["bytes"] / (f16d["ms"] * 1e-3) / 1e9) / hbm if f16d["ms"] else None}
@@ -737,14 +779,13 @@ def main():
                 "mixed_true_rel_residual": stm[-1]["true_rel_residual"],
                 "mixed_rel_err_vs_fp64_x": float(np.linalg.norm(xm - xr) / np.linalg.norm(xr))}
             del p
-        line["mixed_vs_fp64"] = mixed
-        line["batched_multi_rhs"] = batched_block(qcd, torch, flush, hbm, max(2, args.steps // 3))
+        batched = batched_block(qcd, torch, flush, hbm, max(2, args.steps // 3))
         # full-lattice 4^4 normal-equation solve
         p4 = Problem(qcd, "4^4")
         t4 = timed_steps(torch, lambda: p4.solve(qcd, eo=False, normal=True), args.steps, flush)
         line["full_4x4_normal_solves_s"] = args.steps / float(np.sum(t4))
         del p4
-        line["serving"] = serving_block(qcd, torch, n_requests=args.serve_requests)
+        serving = serving_block(qcd, torch, n_requests=args.serve_requests)
         line["dslash_ks_sweep"] = dslash_ks_sweep(qcd, torch, flush, hbm)
         host_fields = {}
         line["dslash_sweep"] = dslash_sweep(qcd, torch, flush, hbm, fields=host_fields)
@@ -764,6 +805,16 @@ def main():
         except Exception as e:  # the oracle is a baseline, not the product
             line["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
                                     "sample": f"not run: {e}"}
+        # the full blocks, then short summaries of the metric's second half as
+        # the last keys of the line (a reader of its tail sees them)
+        line["mixed_vs_fp64_detail"] = mixed
+        line["batched_multi_rhs_detail"] = batched
+        line["serving_detail"] = serving
+        line["dslash_48x48x48x12_frac_hbm"] = {k: v["frac_hbm"] for k, v in line["dslash_sweep"]["48x48x48x12"].items()
+                                               if k in ("f32_r12", "f16_r12", "bf16_r12")}
+        line["batched_multi_rhs"] = batched_summary(batched)
+        line["serving"] = serving_summary(serving)
+        line["mixed_vs_fp64"] = mixed_summary(mixed)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

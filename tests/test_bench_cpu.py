@@ -90,3 +90,36 @@ def test_clock_summary_of_nvidia_smi_rows():
     out = bench.summarize_clocks([busy, hot, hot])
     assert out["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"] and out["sm_mhz"] == 1500.0
     assert bench.summarize_clocks(["", "x, y"]) is None
+
+
+def test_metric_summaries_are_short_and_last():
+    """The mixed-vs-FP64, serving and batching summaries that end the JSON
+    line keep the numbers a reader of the line's tail needs, in a few hundred
+    characters."""
+    sys.path.insert(0, ROOT)
+    import bench
+    mixed = {"24^3x8 Wilson k=0.155": {"fp64_solves_s": 59.71, "mixed_f16_solves_s": 165.3, "ratio": 2.768,
+                                       "mixed_true_rel_residual": 9.1e-11, "fp64_true_rel_residual": 8.7e-11},
+             "48^3x12 twisted mass k=0.16 mu=0.01": {"fp64_solves_s": 6.07, "mixed_f16_solves_s": 17.2,
+                                                     "ratio": 2.834, "mixed_true_rel_residual": 9.9e-11,
+                                                     "fp64_true_rel_residual": 9.2e-11}}
+    m = bench.mixed_summary(mixed)
+    assert m["24^3x8"] == {"fp64": 59.71, "f16_mixed": 165.3, "ratio": 2.77, "max_res": 9.1e-11}
+    assert m["48^3x12 tm"]["ratio"] == 2.83
+    sv = {"requests": 2000, "arrival_rate_per_s": 30.0, "solves_s": 29.81, "latency_p50_ms": 40.12,
+          "latency_p99_ms": 490.4, "failed": 0, "max_true_rel_residual": 9.96e-11}
+    s = bench.serving_summary(sv)
+    assert s["failed"] == 0 and s["p99_ms"] == 490.0 and s["p50_ms"] == 40.1
+    b = {"solve": {"speedup": 0.981, "batched_solves_s": 76.2, "max_true_rel_residual": 9e-11},
+         "kappa_batch": {"speedup": 0.731, "max_true_rel_residual": 9.5e-11},
+         "dslash_f32_r12": {"rhs_per_s_16rhs": 92700.0, "rhs_per_s_1rhs": 43000.0}}
+    bb = bench.batched_summary(b)
+    assert bb["dslash_f32_r12_rhs_speedup"] == 2.16 and bb["max_res"] == 9.5e-11
+    assert len(json.dumps({"batched_multi_rhs": bb, "serving": s, "mixed_vs_fp64": m})) < 700
+
+
+def test_both_arms_share_the_config():
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.workload_config()
+    assert c == bench.workload_config() and c["lattice"] == [24, 24, 24, 8] and c["tol"] == 1e-10

@@ -18,6 +18,7 @@ import pytest
 import oracle
 from paper_1411_5219_gb300 import synthetic as syn
 from tests import _fields as F
+from tests._solves import schur_residual_oracle, sources_12_point_4_gauss
 
 pytestmark = pytest.mark.gpu
 
@@ -219,17 +220,6 @@ def test_invalid_arguments_rejected(q):
 
 
 # --------------------------------------------------------------------- solves
-
-def schur_residual_oracle(U, b, x, kappa, mu):
-    """|Mhat^dag b' - Mhat^dag Mhat x_e| / |Mhat^dag b'| from oracle operators."""
-    be, bo = syn.to_half(b, 0), syn.to_half(b, 1)
-    a = 2 * kappa * mu
-    bp = be + kappa * oracle.dhop_eo(U, oracle.twist(bo, a, inverse=True), 0)
-    rhs = oracle.apply_mhat(U, bp, kappa, mu, dagger=True)
-    xe = syn.to_half(x, 0)
-    lhs = oracle.apply_mhat(U, oracle.apply_mhat(U, xe, kappa, mu), kappa, mu, dagger=True)
-    return F.rel_err(lhs, rhs)
-
 
 def test_solve_full_normal_4x4_config(q):
     """4^4, kappa = 0.15, antiperiodic t, eps = 0.3: CG on M^dag M x = b."""
@@ -547,12 +537,6 @@ def test_df64_recon12_rejected(q):
 
 
 # ------------------------------------------------------ batched multi-RHS
-
-def sources_12_point_4_gauss(dims, seed):
-    srcs = [syn.point_source(dims, s_, c_) for s_ in range(4) for c_ in range(3)]
-    srcs += [syn.gaussian_spinor(dims, seed + k) for k in range(4)]
-    return srcs
-
 
 @pytest.mark.parametrize("prec,recon", [("f64", 18), ("f32", 12), ("f16", 12), ("df64", 18)])
 @pytest.mark.parametrize("nrhs", [16, 3])

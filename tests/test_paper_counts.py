@@ -6,7 +6,8 @@ neighbour fields + the output field, with no reuse of neighbours.  Flops: 8
 SU(3) matrix-vector products (66 flop each) and the vector sums; for Wilson
 the paper's 1632 also counts the spin projection, reconstruction and a
 complex scale per hop (8 x 204), against the 1320 this library reports as
-useful (reading 15)."""
+useful; that breakdown of the paper's figure is an inference, since the
+paper gives none."""
 
 import os
 
