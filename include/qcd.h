@@ -64,6 +64,7 @@ typedef int qcd_status;
 #define QCD_ERR_NOT_CONVERGED 4 /* maxiter reached; x and stats still written */
 #define QCD_ERR_BREAKDOWN 5     /* CG breakdown: <p,Ap> <= 0 or non-finite values */
 #define QCD_ERR_TIMEOUT 6       /* reserved for bounded device waits */
+#define QCD_ERR_CANCELLED 7     /* a queued server request dropped by qcd_server_destroy */
 
 /* Storage precision of a field.  F64/F32/F16/BF16 are IEEE formats (F16
  * spinors carry an FP32 per-site scale).  DF64 ("double-float") stores each
@@ -242,7 +243,7 @@ typedef struct {
     double kappa;          /* hopping parameter */
     double mu;             /* twisted mass (0: Wilson) */
     double tol;            /* target relative residual (e.g. 1e-10) */
-    int maxiter;           /* CG iteration cap */
+    int maxiter;           /* CG iteration cap, 1 .. 2^30 */
     int eo;                /* 1: even-odd Schur complement (solves M x = b) */
     int normal;            /* eo = 0 only: 1 solves M^dagger M x = b, 0 solves M x = b (CGNR) */
     qcd_prec inner_prec;   /* F64: plain FP64 CG; F32/F16/BF16/DF64: inner iterations in that precision with FP64
@@ -344,8 +345,11 @@ qcd_status qcd_server_submit(qcd_server *sv, const qcd_request *req, long long *
 qcd_status qcd_server_wait(qcd_server *sv, long long request_id, qcd_request_result *out);
 /* Bytes reserved by solver contexts, queued and running request counts. */
 qcd_status qcd_server_info(qcd_server *sv, size_t *used_bytes, int *queued, int *running);
-/* Stop the workers (after their current request) and free the contexts;
- * requests not yet waited for are dropped. */
+/* Stop the server: queued requests end with QCD_ERR_CANCELLED (a thread
+ * blocked in qcd_server_wait on one returns with that status), running
+ * requests finish, and the call returns once no thread is inside
+ * qcd_server_wait; then the contexts are freed.  Requests not yet waited for
+ * are dropped.  No call may use the handle after this one has begun. */
 void qcd_server_destroy(qcd_server *sv);
 
 /* ------------------------------------------------------------ measurement */
@@ -379,6 +383,14 @@ qcd_status qcd_profile_begin(void);
 qcd_status qcd_profile_end(qcd_profile *out);
 /* Number of CUDA kernels this library has launched since it was loaded. */
 unsigned long long qcd_kernel_launches(void);
+
+/* Host-side failure injection for tests of the error paths (no device
+ * fault is involved): the next `count` calls of kind `what` fail with
+ * QCD_ERR_OOM before touching the device.  QCD_INJECT_SPINOR_CREATE:
+ * qcd_spinor_create.  count = 0 clears.  The paper has no counterpart (its
+ * Sec. 5 asks that every part of the code be testable on its own). */
+#define QCD_INJECT_SPINOR_CREATE 1
+qcd_status qcd_debug_inject(int what, int count);
 
 #ifdef __cplusplus
 }

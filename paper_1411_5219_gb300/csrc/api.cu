@@ -24,6 +24,19 @@ std::shared_mutex &device_mutex()
 
 void note_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 
+// ---- host-side failure injection (qcd_debug_inject): the next `count`
+// calls of the chosen kind fail as if their allocation had failed
+static std::atomic<int> g_inject[2] = {};
+
+static bool take_injected_failure(int what)
+{
+    std::atomic<int> &n = g_inject[what];
+    int v = n.load();
+    while (v > 0)
+        if (n.compare_exchange_weak(v, v - 1)) return true;
+    return false;
+}
+
 // ---- hopping-kernel profiling (qcd_profile_begin / qcd_profile_end)
 struct ProfRec {
     cudaEvent_t e0, e1;
@@ -499,6 +512,7 @@ cudaError_t hop(const qcd_lattice *lat, const GaugeView &U, int recon, const Hop
     a.state = lat->state;
     a.red_out = lat->red_out;
     a.check_status = h.check_status;
+    a.run_status = h.run_status;
     const bool prof = g_prof_on;
     if (!prof) {
         note_launches();
@@ -539,6 +553,7 @@ const char *qcd_status_string(qcd_status s)
     case QCD_ERR_NOT_CONVERGED: return "QCD_ERR_NOT_CONVERGED";
     case QCD_ERR_BREAKDOWN: return "QCD_ERR_BREAKDOWN";
     case QCD_ERR_TIMEOUT: return "QCD_ERR_TIMEOUT";
+    case QCD_ERR_CANCELLED: return "QCD_ERR_CANCELLED";
     default: return "QCD_ERR_UNKNOWN";
     }
 }
@@ -548,6 +563,14 @@ const char *qcd_last_error(void) { return g_err; }
 const char *qcd_version(void) { return "libqcd 0.1 (sm_103a)"; }
 
 unsigned long long qcd_kernel_launches(void) { return g_launches.load(); }
+
+qcd_status qcd_debug_inject(int what, int count)
+{
+    if (what != QCD_INJECT_SPINOR_CREATE || count < 0)
+        return fail(QCD_ERR_INVALID_ARG, "debug_inject: unknown kind %d or negative count", what);
+    g_inject[what].store(count);
+    return QCD_OK;
+}
 
 qcd_status qcd_profile_begin(void)
 {
@@ -773,6 +796,8 @@ qcd_status qcd_spinor_create(const qcd_lattice *lat, qcd_parity parity, qcd_prec
     if (!lat || !out) return fail(QCD_ERR_INVALID_ARG, "spinor_create: NULL argument");
     *out = nullptr;
     if (!valid_prec(prec) || parity < 0 || parity > 2) return fail(QCD_ERR_INVALID_ARG, "spinor_create: bad prec/parity");
+    if (take_injected_failure(QCD_INJECT_SPINOR_CREATE))
+        return fail(QCD_ERR_OOM, "spinor_create: injected allocation failure");
     qcd_spinor *s = new_spinor(lat, parity, prec);
     if (!s) return fail(QCD_ERR_OOM, "spinor_create: host allocation");
     const int nh = parity == QCD_PARITY_FULL ? 2 : 1;

@@ -277,6 +277,33 @@ __global__ void __launch_bounds__(kThreads) cg_true_residual_kernel(const FieldV
     grid_reduce_rhs<1>(v, rhs.rhs_log2, red, FIN_CG_TRUE, stt, nullptr);
 }
 
+// rho = rhs0 - q (FP64 defect of the un-normalised system), rs = cast(rho)
+template <typename SS>
+__global__ void __launch_bounds__(kThreads) cg_defect_kernel(const FieldView rhs0, const FieldView q,
+                                                             const FieldView rho, const FieldView rs)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nsites(rhs0)) return;
+    Spinor<double> a = ld<SpF64>(rhs0, k);
+    const Spinor<double> b = ld<SpF64>(q, k);
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) a.c[s][c] = a.c[s][c] - b.c[s][c];
+    st<SpF64>(rho, k, a);
+    st<SS>(rs, k, cvt<typename SS::R>(a));
+}
+
+// |f|^2 per rhs (FP64) -> FIN_CG_TRUE, only while the state is CG_VERIFY
+__global__ void __launch_bounds__(kThreads) cg_verify_kernel(const FieldView f, const Reduction red, CgState *stt)
+{
+    if (stt->status != CG_VERIFY) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    double v[1] = {0.0};
+    if (k < nsites(f)) v[0] = norm2(ld<SpF64>(f, k));
+    grid_reduce_rhs<1>(v, f.rhs_log2, red, FIN_CG_TRUE, stt, nullptr);
+}
+
 // batched[(i << L) | rhs] <-> plain[i] over both halves
 template <typename SF>
 __global__ void __launch_bounds__(kThreads) batch_copy_kernel(const FieldView b, const FieldView pl, const int rhs,
@@ -445,6 +472,22 @@ cudaError_t launch_cg_p(const FieldView &p, const FieldView &r, CgState *stt, cu
 cudaError_t launch_cg_accum_x(const FieldView &xhi, const FieldView &xs, cudaStream_t s)
 {
     QCD_SP_CASES(xs.prec, SS, cg_accum_x_kernel<SS><<<grid_of(xhi), kThreads, 0, s>>>(xhi, xs));
+    note_launches();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_defect(const FieldView &rhs0, const FieldView &q, const FieldView &rho, const FieldView &rs,
+                             cudaStream_t s)
+{
+    QCD_SP_CASES(rs.prec, SS, cg_defect_kernel<SS><<<grid_of(rhs0), kThreads, 0, s>>>(rhs0, q, rho, rs));
+    note_launches();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_verify(const FieldView &f, const Reduction &red, CgState *stt, cudaStream_t s)
+{
+    if (!reduction_fits(red, 1, f.rhs_log2, grid_of(f).x)) return cudaErrorInvalidValue;
+    cg_verify_kernel<<<grid_of(f), kThreads, 0, s>>>(f, red, stt);
     note_launches();
     return cudaGetLastError();
 }

@@ -20,6 +20,7 @@
 #pragma once
 
 #include "qcd_internal.cuh"
+#include "dslash_pairs.cuh"
 
 namespace qcd {
 
@@ -269,11 +270,12 @@ __host__ __device__ constexpr int dslash_min_blocks_tpb()
     return sizeof(typename SF::R) == 8 && GF::kRecon_ != 8 ? (TPB == 64 ? 6 : 1) : 1;
 }
 
-template <typename SF, typename GF, int kDagger, int kEpi, bool kReduce, int TPB>
-__global__ void __launch_bounds__(TPB, (dslash_min_blocks_tpb<SF, GF, TPB>())) dslash_kernel(const DslashLaunch a)
+template <typename SF, typename GF, int kDagger, int kEpi, bool kReduce, int TPB,
+          int kMinBlocks = dslash_min_blocks_tpb<SF, GF, TPB>()>
+__global__ void __launch_bounds__(TPB, kMinBlocks) dslash_kernel(const DslashLaunch a)
 {
     using R = typename SF::R;
-    if (a.check_status && a.state->status != CG_RUNNING) return;
+    if (a.check_status && a.state->status != a.run_status) return;
     constexpr int SF_ = kDagger ? -1 : +1;  // projector sign of forward hops
     constexpr int SB_ = -SF_;                // ... of backward hops
     // element e = site i * 2^rhs_log2 + rhs (one rhs: e = i)
@@ -336,7 +338,34 @@ __global__ void __launch_bounds__(TPB, (dslash_min_blocks_tpb<SF, GF, TPB>())) d
             ru = ru_n;                                                     \
         }                                                                  \
     }
-        if constexpr (!std::is_same<R, double>::value) {
+        if constexpr (is_sp16<SF>::value) {
+            // 16-bit spinors: packed FP32 arithmetic on the two spins
+            AccPairs ap;
+#define QCD_HOP16(K, MU, S, ADJ, FIRST)                                      \
+    {                                                                      \
+        typename SF::Raw rs_n;                                             \
+        typename GF::Raw ru_n;                                             \
+        if (K < 7) {                                                       \
+            rs_n = SF::fetch(in, nb[(K + 1) & 7]);                         \
+            ru_n = GF::fetch(a.U, lb[(K + 1) & 7], li[(K + 1) & 7]);       \
+        }                                                                  \
+        hop_pairs<SF, GF, MU, S, ADJ, FIRST>(ap, rs, ru, fl[K]);           \
+        if (K < 7) {                                                       \
+            rs = rs_n;                                                     \
+            ru = ru_n;                                                     \
+        }                                                                  \
+    }
+            QCD_HOP16(0, 0, SF_, false, true)
+            QCD_HOP16(1, 0, SB_, true, false)
+            QCD_HOP16(2, 1, SF_, false, false)
+            QCD_HOP16(3, 1, SB_, true, false)
+            QCD_HOP16(4, 2, SF_, false, false)
+            QCD_HOP16(5, 2, SB_, true, false)
+            QCD_HOP16(6, 3, SF_, false, false)
+            QCD_HOP16(7, 3, SB_, true, false)
+#undef QCD_HOP16
+            acc = unpair(ap);
+        } else if constexpr (!std::is_same<R, double>::value) {
             QCD_HOP(0, 0, SF_, false, true)
             QCD_HOP(1, 0, SB_, true, false)
             QCD_HOP(2, 1, SF_, false, false)

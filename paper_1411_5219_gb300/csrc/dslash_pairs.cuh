@@ -1,0 +1,207 @@
+// The hop of the 16-bit hopping kernels in packed FP32 arithmetic.
+//
+// The two spin components of a half spinor are multiplied by the same link,
+// so they form the two lanes of an FP32 pair: every multiply-add of the
+// SU(3) product, of the spin projection and of the accumulation of the upper
+// spins acts on both spins at once (one fma.rn.f32x2 instead of two FMAs).
+// The operation is the one of dslash_kernel.cuh (the Wilson hop of CL2QCD,
+// arXiv:1411.5219, Sec. 1): h = psi_up - S B psi_dn projected, U h or
+// U^dagger h, lower spins rebuilt as -S B^dagger (U h), with the chiral
+// basis gamma_mu = [[0, B], [B^dagger, 0]].
+//
+// Pair layout: lane 0 holds spin 0 (upper) or spin 2 (lower), lane 1 spin 1
+// or spin 3.  Real and imaginary parts are kept in separate pairs.
+#pragma once
+
+#include "qcd_internal.cuh"
+
+namespace qcd {
+
+template <typename SF>
+struct is_sp16 : std::false_type {};
+template <typename H, bool N>
+struct is_sp16<Sp16<H, N>> : std::true_type {};
+
+__device__ __forceinline__ float2 bc(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 swp(float2 a) { return make_float2(a.y, a.x); }
+
+// 16-bit (re, im) word -> FP32 parts
+template <typename H>
+struct Half16Parts;
+template <>
+struct Half16Parts<__half> {
+    __device__ __forceinline__ static float re(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu))); }
+    __device__ __forceinline__ static float im(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w >> 16))); }
+};
+template <>
+struct Half16Parts<__nv_bfloat16> {
+    __device__ __forceinline__ static float re(uint32_t w) { return __uint_as_float(w << 16); }
+    __device__ __forceinline__ static float im(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+};
+
+// Half spinor in pairs: hr[c] = (Re h0_c, Re h1_c), hi[c] = (Im h0_c, Im h1_c).
+struct HalfPairs {
+    float2 r[3], i[3];
+};
+
+// Accumulated spinor in pairs: u* = spins (0, 1), l* = spins (2, 3).
+struct AccPairs {
+    float2 ur[3], ui[3], lr[3], li[3];
+};
+
+template <typename H>
+__device__ __forceinline__ uint32_t word16(const uint4 (&w)[3], int k)
+{
+    const uint4 &p = w[k >> 2];
+    return (k & 3) == 0 ? p.x : (k & 3) == 1 ? p.y : (k & 3) == 2 ? p.z : p.w;
+}
+
+// Spin projection of a 16-bit spinor (unscaled) straight from its words:
+// lane 0 is h_0 = psi_0 + ..., lane 1 is h_1 = psi_1 + ...; the lower spins
+// enter in the order (3, 2) for x and y, (2, 3) for z and t.
+template <typename H, int MU, int S>
+__device__ __forceinline__ HalfPairs project_pairs(const uint4 (&w)[3])
+{
+    using P = Half16Parts<H>;
+    constexpr int b0 = MU <= 1 ? 3 : 2, b1 = MU <= 1 ? 2 : 3;
+    constexpr float s = (float)S;
+    HalfPairs h;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const uint32_t a0 = word16<H>(w, c), a1 = word16<H>(w, 3 + c);
+        const uint32_t x0 = word16<H>(w, 3 * b0 + c), x1 = word16<H>(w, 3 * b1 + c);
+        const float2 ar = make_float2(P::re(a0), P::re(a1)), ai = make_float2(P::im(a0), P::im(a1));
+        const float2 xr = make_float2(P::re(x0), P::re(x1)), xi = make_float2(P::im(x0), P::im(x1));
+        if (MU == 0) {  // h = (psi0 + S i psi3, psi1 + S i psi2)
+            h.r[c] = fma2(xi, make_float2(-s, -s), ar);
+            h.i[c] = fma2(xr, make_float2(s, s), ai);
+        } else if (MU == 1) {  // h = (psi0 + S psi3, psi1 - S psi2)
+            h.r[c] = fma2(xr, make_float2(s, -s), ar);
+            h.i[c] = fma2(xi, make_float2(s, -s), ai);
+        } else if (MU == 2) {  // h = (psi0 + S i psi2, psi1 - S i psi3)
+            h.r[c] = fma2(xi, make_float2(-s, s), ar);
+            h.i[c] = fma2(xr, make_float2(s, -s), ai);
+        } else {  // h = (psi0 - S psi2, psi1 - S psi3)
+            h.r[c] = fma2(xr, make_float2(-s, -s), ar);
+            h.i[c] = fma2(xi, make_float2(-s, -s), ai);
+        }
+    }
+    return h;
+}
+
+// U h (kAdj false) or U^dagger h (kAdj true) on both spins.
+template <bool kAdj>
+__device__ __forceinline__ HalfPairs su3_pairs(const Link<float> &u, const HalfPairs &h)
+{
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    HalfPairs v;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (!kAdj) {
+            // Re = sum Re U Re h - Im U Im h ; Im = sum Re U Im h + Im U Re h
+            float2 p = mul2(bc(u.m[a][0].re), h.r[0]);
+            float2 q = mul2(bc(u.m[a][0].im), h.i[0]);
+            float2 t = mul2(bc(u.m[a][0].re), h.i[0]);
+            t = fma2(bc(u.m[a][0].im), h.r[0], t);
+#pragma unroll
+            for (int j = 1; j < 3; ++j) {
+                p = fma2(bc(u.m[a][j].re), h.r[j], p);
+                q = fma2(bc(u.m[a][j].im), h.i[j], q);
+                t = fma2(bc(u.m[a][j].re), h.i[j], t);
+                t = fma2(bc(u.m[a][j].im), h.r[j], t);
+            }
+            v.r[a] = fma2(q, m1, p);
+            v.i[a] = t;
+        } else {
+            // Re = sum Re U_ja Re h + Im U_ja Im h ; Im = sum Re U_ja Im h - Im U_ja Re h
+            float2 t = mul2(bc(u.m[0][a].re), h.r[0]);
+            t = fma2(bc(u.m[0][a].im), h.i[0], t);
+            float2 p = mul2(bc(u.m[0][a].re), h.i[0]);
+            float2 q = mul2(bc(u.m[0][a].im), h.r[0]);
+#pragma unroll
+            for (int j = 1; j < 3; ++j) {
+                t = fma2(bc(u.m[j][a].re), h.r[j], t);
+                t = fma2(bc(u.m[j][a].im), h.i[j], t);
+                p = fma2(bc(u.m[j][a].re), h.i[j], p);
+                q = fma2(bc(u.m[j][a].im), h.r[j], q);
+            }
+            v.r[a] = t;
+            v.i[a] = fma2(q, m1, p);
+        }
+    }
+    return v;
+}
+
+// acc (+)= w * (the full spinor rebuilt from v): upper = v, lower =
+// -S B^dagger v.  In pairs the lower spins of x and y take v with its lanes
+// swapped (spin 2 gains from spin 1 and spin 3 from spin 0).
+template <int MU, int S, bool kFirst>
+__device__ __forceinline__ void accumulate_pairs(AccPairs &acc, const HalfPairs &v, float w)
+{
+    const float ws = w * (float)S;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float2 lr_w, li_w, lr_v, li_v;  // lower += lr_w * lr_v (real), li_w * li_v (imag)
+        if (MU == 0) {  // (l2, l3) = -S (i u1, i u0)
+            lr_v = swp(v.i[c]);
+            lr_w = bc(ws);
+            li_v = swp(v.r[c]);
+            li_w = bc(-ws);
+        } else if (MU == 1) {  // (l2, l3) = -S (u1, -u0)
+            lr_v = swp(v.r[c]);
+            li_v = swp(v.i[c]);
+            lr_w = li_w = make_float2(-ws, ws);
+        } else if (MU == 2) {  // (l2, l3) = -S (i u0, -i u1)
+            lr_v = v.i[c];
+            lr_w = make_float2(ws, -ws);
+            li_v = v.r[c];
+            li_w = make_float2(-ws, ws);
+        } else {  // (l2, l3) = -S (u0, u1)
+            lr_v = v.r[c];
+            li_v = v.i[c];
+            lr_w = li_w = bc(-ws);
+        }
+        if (kFirst) {
+            acc.ur[c] = mul2(bc(w), v.r[c]);
+            acc.ui[c] = mul2(bc(w), v.i[c]);
+            acc.lr[c] = mul2(lr_w, lr_v);
+            acc.li[c] = mul2(li_w, li_v);
+        } else {
+            acc.ur[c] = fma2(bc(w), v.r[c], acc.ur[c]);
+            acc.ui[c] = fma2(bc(w), v.i[c], acc.ui[c]);
+            acc.lr[c] = fma2(lr_w, lr_v, acc.lr[c]);
+            acc.li[c] = fma2(li_w, li_v, acc.li[c]);
+        }
+    }
+}
+
+// One hop of a 16-bit spinor: project, multiply, rebuild and accumulate;
+// `flip` applies the boundary factor -1 (folded into the weight with the
+// FP16 per-site scale).
+template <typename SF, typename GF, int MU, int S, bool kAdj, bool kFirst>
+__device__ __forceinline__ void hop_pairs(AccPairs &acc, const typename SF::Raw &rs, const typename GF::Raw &ru,
+                                          bool flip)
+{
+    using H = typename SF::H16;
+    const HalfPairs h = project_pairs<H, MU, S>(rs.w);
+    const HalfPairs v = su3_pairs<kAdj>(GF::decode(ru), h);
+    const float sc = SF::scale(rs);
+    accumulate_pairs<MU, S, kFirst>(acc, v, flip ? -sc : sc);
+}
+
+__device__ __forceinline__ Spinor<float> unpair(const AccPairs &a)
+{
+    Spinor<float> s;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        s.c[0][c] = mk(a.ur[c].x, a.ui[c].x);
+        s.c[1][c] = mk(a.ur[c].y, a.ui[c].y);
+        s.c[2][c] = mk(a.lr[c].x, a.li[c].x);
+        s.c[3][c] = mk(a.lr[c].y, a.li[c].y);
+    }
+    return s;
+}
+
+}  // namespace qcd

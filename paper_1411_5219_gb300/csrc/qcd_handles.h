@@ -123,6 +123,7 @@ struct HopArgs {
     const Reduction *red;  // scratch of the fused reduction (nullptr: the lattice's)
     const double *coef;    // device table of cy, cd (8 doubles) read at run time, or nullptr
     int coef_stride;       // doubles between the tables of consecutive rhs (0: shared)
+    int run_status;        // with check_status: run only under this CG status (default CG_RUNNING = 0)
 };
 cudaError_t hop(const qcd_lattice *lat, const GaugeView &U, int recon, const HopArgs &h, cudaStream_t s);
 

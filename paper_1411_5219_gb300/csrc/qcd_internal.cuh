@@ -275,6 +275,7 @@ struct SpDF64 {
 template <typename H, bool kNorm>
 struct Sp16 {
     using R = float;
+    using H16 = H;
     static constexpr int kPlanes = 3;
     static constexpr size_t kBytesPerSite = 48 + (kNorm ? 4 : 0);
     // decode() leaves the FP16 per-site scale out; scale() returns it, so the
@@ -840,6 +841,7 @@ enum CgStatus : int {
     CG_BREAKDOWN = 3,   // <p, A p> <= 0 or non-finite values
     CG_MAXITER = 4,     // (global)
     CG_DONE = 5,        // true residual below the target
+    CG_VERIFY = 6,      // (global) an inner-precision estimate of the true residual met a target: check in FP64
 };
 
 constexpr int kMaxRhs = 32;
@@ -876,6 +878,7 @@ enum FinalizeKind : int {
     FIN_CG_RR = 2,      // rr_new = total; beta, convergence, reliable trigger
     FIN_CG_TRUE = 3,    // true residual after a reliable update
     FIN_CG_INIT = 4,    // |rhs|^2 at the start of CG
+    FIN_CG_TRUE_EST = 5,// true residual estimated in the inner precision (Mhat^dag of the FP64 defect)
 };
 
 // tot[r] = the reduced value of right-hand side r (first value only).
@@ -944,8 +947,33 @@ __device__ __forceinline__ void cg_finalize_rhs(FinalizeKind kind, const double 
             st->status = CG_RELIABLE;
         else if (st->iter >= st->maxiter)
             st->status = CG_MAXITER;
-    } else if (kind == FIN_CG_TRUE) {
+    } else if (kind == FIN_CG_TRUE_EST) {
+        // The FP64 defect rho = rhs0 - Mhat x, mapped by Mhat^dag in a lower
+        // precision: a system whose estimate meets its target is checked in
+        // FP64 next (CG_VERIFY); the others continue from the estimate.
         st->reliable_updates += 1;
+        bool verify = false, bad = false;
+        for (int k = 0; k < n; ++k) {
+            CgRhs &q = st->r[k];
+            if (q.status == CG_DONE) {
+                q.beta = 0.0;
+                continue;
+            }
+            const double rt = tot[k];
+            q.rr_true = rt;
+            if (!isfinite(rt)) {
+                bad = true;
+            } else if (rt <= q.rr_stop) {
+                verify = true;
+            } else {
+                q.beta = rt / q.rr_prev;
+                q.rr = rt;
+                q.rr_max = rt;
+            }
+        }
+        st->status = bad ? CG_BREAKDOWN : verify ? CG_VERIFY : (st->iter >= st->maxiter ? CG_MAXITER : CG_RUNNING);
+    } else if (kind == FIN_CG_TRUE) {
+        if (st->status != CG_VERIFY) st->reliable_updates += 1;  // (a verification completes its update)
         bool all_done = true, bad = false;
         for (int k = 0; k < n; ++k) {
             CgRhs &q = st->r[k];
@@ -1093,9 +1121,10 @@ struct DslashLaunch {
     bool reduce;
     Reduction red;
     FinalizeKind fin;
-    CgState *state;     // also: early exit when state->status != RUNNING (if check_status)
+    CgState *state;     // also: early exit when state->status != run_status (if check_status)
     double *red_out;
     bool check_status;
+    int run_status;     // the status the launch runs under (CG_RUNNING, or CG_VERIFY for a check)
 };
 
 cudaError_t launch_dslash(int prec, int recon, const DslashLaunch &a, cudaStream_t s);

@@ -51,6 +51,11 @@ cudaError_t launch_cg_xr(const FieldView &x, const FieldView &p, const FieldView
 cudaError_t launch_cg_p(const FieldView &p, const FieldView &r, CgState *st, cudaStream_t s);
 // xhi += xs, xs = 0 (mixed precision, before a reliable update)
 cudaError_t launch_cg_accum_x(const FieldView &xhi, const FieldView &xs, cudaStream_t s);
+// rho = rhs0 - q (F64 defect of the un-normalised system) and rs = cast(rho).
+cudaError_t launch_cg_defect(const FieldView &rhs0, const FieldView &q, const FieldView &rho, const FieldView &rs,
+                             cudaStream_t s);
+// |f|^2 (F64) -> FIN_CG_TRUE, only while the CG state is CG_VERIFY.
+cudaError_t launch_cg_verify(const FieldView &f, const Reduction &red, CgState *st, cudaStream_t s);
 // rhi = rhs - q (F64), |rhi|^2 -> reliable-update decision; rs = cast(rhi) if given.
 cudaError_t launch_cg_true_residual(const FieldView &rhs, const FieldView &q, const FieldView &rhi,
                                    const FieldView *rs, const Reduction &red, CgState *st, cudaStream_t s);

@@ -74,8 +74,9 @@ struct qcd_server {
     std::map<long long, Job *> jobs;
     long long next_id = 1;
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
+    std::condition_variable cv_work, cv_done, cv_idle;
     bool stop = false;
+    int waiters = 0;  // threads inside qcd_server_wait
     std::vector<std::thread> workers;
     std::vector<std::map<std::string, VolumeCtx>> slot_ctx;
     std::vector<cudaStream_t> streams;     // per slot, high priority (small volumes)
@@ -125,10 +126,25 @@ void run_job(qcd_server *sv, int s, Job *j)
         c = &sv->slot_ctx[s][dims_key(g->lat)];
     }
     qcd_status st = QCD_OK;
-    if (!c->lat) {
+    if (!c->lat || !c->b || !c->x) {
+        // build the context whole; a part left by an earlier failed build is
+        // dropped first, and a failed build leaves nothing behind (the
+        // reserved bytes stay with the context entry until it is released)
+        qcd_spinor_destroy(c->b);
+        qcd_spinor_destroy(c->x);
+        qcd_lattice_destroy(c->lat);
+        c->lat = nullptr;
+        c->b = c->x = nullptr;
         st = qcd_lattice_create(g->lat->dims, g->lat->t_bc, &c->lat);
         if (st == QCD_OK) st = qcd_spinor_create(c->lat, QCD_PARITY_FULL, QCD_PREC_F64, &c->b);
         if (st == QCD_OK) st = qcd_spinor_create(c->lat, QCD_PARITY_FULL, QCD_PREC_F64, &c->x);
+        if (st != QCD_OK) {
+            qcd_spinor_destroy(c->b);
+            qcd_spinor_destroy(c->x);
+            qcd_lattice_destroy(c->lat);
+            c->lat = nullptr;
+            c->b = c->x = nullptr;
+        }
     }
     // Small volumes run on the slot's high-priority stream, so their few
     // short kernels are not queued behind the long ones of large volumes.
@@ -232,6 +248,7 @@ qcd_status qcd_server_submit(qcd_server *sv, const qcd_request *req, long long *
     if (!sv || !req || !request_id) return fail(QCD_ERR_INVALID_ARG, "server_submit: NULL argument");
     if (!req->b_host || !req->x_host) return fail(QCD_ERR_INVALID_ARG, "server_submit: NULL host buffer");
     std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->stop) return fail(QCD_ERR_INVALID_ARG, "server_submit: the server is being destroyed");
     if (req->gauge_id < 0 || req->gauge_id >= (int)sv->gauges.size())
         return fail(QCD_ERR_INVALID_ARG, "server_submit: unknown gauge id %d", req->gauge_id);
     if (context_bytes(sv->gauges[req->gauge_id]->lat) > sv->budget)
@@ -254,7 +271,9 @@ qcd_status qcd_server_wait(qcd_server *sv, long long request_id, qcd_request_res
     auto it = sv->jobs.find(request_id);
     if (it == sv->jobs.end()) return fail(QCD_ERR_INVALID_ARG, "server_wait: unknown request %lld", request_id);
     Job *j = it->second;
+    ++sv->waiters;
     sv->cv_done.wait(lk, [&] { return j->done; });
+    --sv->waiters;
     out->id = j->id;
     out->status = j->status;
     out->stats = j->stats;
@@ -264,6 +283,7 @@ qcd_status qcd_server_wait(qcd_server *sv, long long request_id, qcd_request_res
     out->slot = j->slot;
     sv->jobs.erase(it);
     delete j;
+    if (sv->stop && sv->waiters == 0) sv->cv_idle.notify_all();
     return QCD_OK;
 }
 
@@ -285,11 +305,26 @@ void qcd_server_destroy(qcd_server *sv)
 {
     if (!sv) return;
     {
+        // queued requests are cancelled; threads waiting for them return
         std::lock_guard<std::mutex> lk(sv->mu);
         sv->stop = true;
+        const double t = sv->now();
+        for (Job *j : sv->queue) {
+            j->status = QCD_ERR_CANCELLED;
+            j->t_start = j->t_end = t;
+            j->done = true;
+        }
+        sv->queue.clear();
         sv->cv_work.notify_all();
+        sv->cv_done.notify_all();
     }
-    for (auto &t : sv->workers) t.join();
+    for (auto &t : sv->workers) t.join();  // running requests finish first
+    {
+        // no thread may still be inside qcd_server_wait when sv is freed
+        std::unique_lock<std::mutex> lk(sv->mu);
+        sv->cv_done.notify_all();
+        sv->cv_idle.wait(lk, [&] { return sv->waiters == 0; });
+    }
     cudaSetDevice(sv->device);
     for (auto &m : sv->slot_ctx)
         for (auto &kv : m) release(sv, kv.second);

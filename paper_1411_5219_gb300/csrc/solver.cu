@@ -44,6 +44,7 @@ struct OpCtx {
 // and the cached CG graph depends on neither.  Blocks of 8 doubles
 // (cy[2][2], cd[2][2]) at these offsets:
 constexpr int kCoefPerRhs = 96;
+constexpr int kMaxIter = 1 << 30;  // largest accepted maxiter
 constexpr int kCoefOp = 0;        // normal operator, 4 hops (2 for the full lattice)
 constexpr int kCoefSrcB = 32;     // b' = b_e + kappa D_eo A^-1 b_o
 constexpr int kCoefSrcT = 40;     // t = A^-dag D_oe^dag b'
@@ -93,70 +94,102 @@ HopArgs table_hop(const OpCtx &c, int off)
     return h;
 }
 
+// How the kernels of one operator application run.
+struct OpRun {
+    bool check = false;              // early exit unless the CG state is run_status
+    int run_status = CG_RUNNING;
+    bool reduce = false;             // |out|^2 of the last kernel -> fin
+    FinalizeKind fin = FIN_STORE;
+};
+
+HopArgs op_hop(const OpCtx &c, int off, const OpRun &r)
+{
+    HopArgs h = table_hop(c, off);
+    h.check_status = r.check;
+    h.run_status = r.run_status;
+    h.fin = r.fin;
+    return h;
+}
+
+// out = Mhat in (eo; t: odd-site temporary) or M in (full).
+cudaError_t apply_fwd(const OpCtx &c, const GaugeView &U, int recon, const FieldView &in, const FieldView &out,
+                      const FieldView &t, const OpRun &r, cudaStream_t st)
+{
+    cudaError_t e;
+    if (c.eo) {
+        HopArgs h = op_hop(c, kCoefOp + 0, r);  // t = A^-1 D_oe in
+        h.out = &t;
+        h.in = &in;
+        h.out_parity = 1;
+        h.plain = !c.tw;
+        if ((e = hop(c.lat, U, recon, h, st)) != cudaSuccess) return e;
+        HopArgs h2 = op_hop(c, kCoefOp + 8, r);  // out = A in - kappa^2 D_eo t
+        h2.out = &out;
+        h2.in = &t;
+        h2.y = &in;
+        h2.out_parity = 0;
+        h2.reduce = r.reduce;
+        h2.red = c.red;
+        return hop(c.lat, U, recon, h2, st);
+    }
+    HopArgs h = op_hop(c, kCoefOp + 0, r);  // out = A in - kappa D in
+    h.out = &out;
+    h.in = &in;
+    h.y = &in;
+    h.both = true;
+    h.reduce = r.reduce;
+    h.red = c.red;
+    return hop(c.lat, U, recon, h, st);
+}
+
+// out = Mhat^dag in (eo; t: odd-site temporary) or M^dag in (full).
+cudaError_t apply_dag(const OpCtx &c, const GaugeView &U, int recon, const FieldView &in, const FieldView &out,
+                      const FieldView &t, const OpRun &r, cudaStream_t st)
+{
+    cudaError_t e;
+    if (c.eo) {
+        HopArgs h = op_hop(c, kCoefOp + 16, r);  // t = A^-dag D_oe^dag in
+        h.out = &t;
+        h.in = &in;
+        h.out_parity = 1;
+        h.dagger = 1;
+        h.plain = !c.tw;
+        if ((e = hop(c.lat, U, recon, h, st)) != cudaSuccess) return e;
+        HopArgs h2 = op_hop(c, kCoefOp + 24, r);  // out = A^dag in - kappa^2 D_eo^dag t
+        h2.out = &out;
+        h2.in = &t;
+        h2.y = &in;
+        h2.out_parity = 0;
+        h2.dagger = 1;
+        h2.reduce = r.reduce;
+        h2.red = c.red;
+        return hop(c.lat, U, recon, h2, st);
+    }
+    HopArgs h = op_hop(c, kCoefOp + 8, r);  // out = M^dag in
+    h.out = &out;
+    h.in = &in;
+    h.y = &in;
+    h.both = true;
+    h.dagger = 1;
+    h.reduce = r.reduce;
+    h.red = c.red;
+    return hop(c.lat, U, recon, h, st);
+}
+
 // out = Mhat^dag Mhat in (eo) or M^dag M in (full).  t (odd half) and s
 // (even half, or full) are temporaries of the same precision.  With
 // reduce_alpha the second kernel also reduces |Mhat in|^2 into alpha.
 cudaError_t apply_normal(const OpCtx &c, const GaugeView &U, int recon, const FieldView &in, const FieldView &out,
                          const FieldView &t, const FieldView &s, bool reduce_alpha, bool check, cudaStream_t st)
 {
-    cudaError_t e;
-    if (c.eo) {
-        // t = A^-1 D_oe in
-        HopArgs h = table_hop(c, kCoefOp + 0);
-        h.check_status = check;
-        h.fin = FIN_CG_ALPHA;
-        h.out = &t;
-        h.in = &in;
-        h.out_parity = 1;
-        h.plain = !c.tw;
-        if ((e = hop(c.lat, U, recon, h, st)) != cudaSuccess) return e;
-        // s = A in - kappa^2 D_eo t   (|s|^2 -> alpha)
-        HopArgs h2 = table_hop(c, kCoefOp + 8);
-        h2.check_status = check;
-        h2.fin = FIN_CG_ALPHA;
-        h2.out = &s;
-        h2.in = &t;
-        h2.y = &in;
-        h2.out_parity = 0;
-        h2.reduce = reduce_alpha;
-        h2.red = c.red;
-        if ((e = hop(c.lat, U, recon, h2, st)) != cudaSuccess) return e;
-        // t = A^-dag D_oe^dag s
-        HopArgs h3 = h;
-        h3.in = &s;
-        h3.dagger = 1;
-        h3.coef = c.coef + kCoefOp + 16;
-        if ((e = hop(c.lat, U, recon, h3, st)) != cudaSuccess) return e;
-        // out = A^dag s - kappa^2 D_eo^dag t
-        HopArgs h4 = h2;
-        h4.out = &out;
-        h4.in = &t;
-        h4.y = &s;
-        h4.dagger = 1;
-        h4.reduce = false;
-        h4.coef = c.coef + kCoefOp + 24;
-        return hop(c.lat, U, recon, h4, st);
-    }
-    // s = M in = A in - kappa D in  (|s|^2 -> alpha)
-    HopArgs h = table_hop(c, kCoefOp + 0);
-    h.check_status = check;
-    h.fin = FIN_CG_ALPHA;
-    h.out = &s;
-    h.in = &in;
-    h.y = &in;
-    h.both = true;
-    h.reduce = reduce_alpha;
-    h.red = c.red;
-    if ((e = hop(c.lat, U, recon, h, st)) != cudaSuccess) return e;
-    // out = M^dag s
-    HopArgs h2 = h;
-    h2.out = &out;
-    h2.in = &s;
-    h2.y = &s;
-    h2.dagger = 1;
-    h2.reduce = false;
-    h2.coef = c.coef + kCoefOp + 8;
-    return hop(c.lat, U, recon, h2, st);
+    OpRun r;
+    r.check = check;
+    r.reduce = reduce_alpha;
+    r.fin = FIN_CG_ALPHA;
+    cudaError_t e = apply_fwd(c, U, recon, in, s, t, r, st);
+    if (e != cudaSuccess) return e;
+    r.reduce = false;
+    return apply_dag(c, U, recon, s, out, t, r, st);
 }
 
 // out = M in on a full field (dagger: M^dag).
@@ -185,6 +218,21 @@ struct CgFields {
     FieldView rs, ps, qs, ts, ss, xs;   // inner (aliases of the FP64 ones when not mixed)
     Reduction red;
     CgState *state;
+    // Split true residual (mixed precision with an un-normalised system
+    // rhs0: b'_e for eo, b for the full-lattice M^dag M x = M^dag b): the
+    // FP64 defect rho = rhs0 - Mhat x is mapped by Mhat^dag in a lower
+    // precision; only an estimate that meets the target is checked with the
+    // FP64 Mhat^dag.
+    bool split;
+    FieldView rhs0;
+    // The precision of the defect's Mhat^dag image: FP32 for 16-bit inner
+    // fields (a 16-bit image would carry cond(Mhat) times the 16-bit
+    // roundoff), else the inner precision.  With FP32 it is cast to the inner
+    // r once.
+    GaugeView Um;
+    int rm_recon;
+    bool mid;               // the image has its own FP32 fields
+    FieldView rho_m, t_m, r_m;
 };
 
 // One CG iteration: q = A p (|Mhat p|^2 -> alpha), x += alpha p, r -= alpha q
@@ -204,6 +252,32 @@ cudaError_t enqueue_iteration(const CgFields &f, cudaStream_t s)
 cudaError_t enqueue_true_residual(const CgFields &f, cudaStream_t s)
 {
     cudaError_t e = cudaSuccess;
+    if (f.split) {
+        // x += xs; rho = rhs0 - Mhat x (FP64, two hops); r_inner = Mhat^dag rho
+        // in FP32 or the inner precision (two hops, |r|^2 -> estimate); under
+        // CG_VERIFY the FP64 Mhat^dag rho and its norm decide; then p = r + beta p.
+        OpRun plain_run;
+        OpRun est;
+        est.reduce = true;
+        est.fin = FIN_CG_TRUE_EST;
+        OpRun check;
+        check.check = true;
+        check.run_status = CG_VERIFY;
+        e = launch_cg_accum_x(f.xh, f.xs, s);
+        if (e == cudaSuccess) e = apply_fwd(f.c, f.Uh, f.rh_recon, f.xh, f.sh, f.th, plain_run, s);
+        if (f.mid) {
+            if (e == cudaSuccess) e = launch_cg_defect(f.rhs0, f.sh, f.rh, f.rho_m, s);
+            if (e == cudaSuccess) e = apply_dag(f.c, f.Um, f.rm_recon, f.rho_m, f.r_m, f.t_m, est, s);
+            if (e == cudaSuccess) e = launch_convert(f.rs, f.r_m, s);
+        } else {
+            if (e == cudaSuccess) e = launch_cg_defect(f.rhs0, f.sh, f.rh, f.ss, s);
+            if (e == cudaSuccess) e = apply_dag(f.c, f.Us, f.rs_recon, f.ss, f.rs, f.ts, est, s);
+        }
+        if (e == cudaSuccess) e = apply_dag(f.c, f.Uh, f.rh_recon, f.rh, f.qh, f.th, check, s);
+        if (e == cudaSuccess) e = launch_cg_verify(f.qh, f.red, f.state, s);
+        if (e == cudaSuccess) e = launch_cg_p(f.ps, f.rs, f.state, s);
+        return e;
+    }
     if (f.mixed) e = launch_cg_accum_x(f.xh, f.xs, s);
     if (e == cudaSuccess) e = apply_normal(f.c, f.Uh, f.rh_recon, f.xh, f.qh, f.th, f.sh, false, false, s);
     if (e == cudaSuccess) e = launch_cg_true_residual(f.rhs, f.qh, f.rh, f.mixed ? &f.rs : nullptr, f.red, f.state, s);
@@ -277,7 +351,8 @@ qcd_status cg_graph(const qcd_lattice *lat, const CgFields &f, cudaGraphExec_t *
              f.rs.hv[0].data, f.ps.hv[0].data, f.qs.hv[0].data, f.ts.hv[0].data, f.ss.hv[0].data, f.xs.hv[0].data,
              (void *)f.state, f.rs.prec, f.rhs.nh);
     const size_t used = strlen(key);
-    snprintf(key + used, sizeof(key) - used, "|%p|%d", (void *)f.red.partials, f.rs.rhs_log2);
+    snprintf(key + used, sizeof(key) - used, "|%p|%d|%d|%p|%d|%p|%p", (void *)f.red.partials, f.rs.rhs_log2,
+             (int)f.split, f.rhs0.hv[0].data, (int)f.mid, f.Um.data, f.r_m.hv[0].data);
     auto it = lat->graphs.find(key);
     if (it != lat->graphs.end()) {
         it->second.last_use = ++lat->graph_clock;
@@ -417,8 +492,11 @@ qcd_status qcd::solve_impl(const qcd_gauge *g, qcd_spinor *const *x, const qcd_s
     if (g->prec != QCD_PREC_F64) return fail(QCD_ERR_INVALID_ARG, "solve_cg: the gauge field must be F64");
     for (int k = 0; k < nrhs; ++k) {
         const qcd_solver_params &q = prm[k];
-        if (!(q.tol > 0.0) || q.maxiter < 1 || !std::isfinite(q.kappa) || !std::isfinite(q.mu))
-            return fail(QCD_ERR_INVALID_ARG, "solve_cg: bad tol/maxiter/kappa/mu (system %d)", k);
+        // the device loop's trip cap is maxiter + 64 in 32-bit arithmetic
+        if (!(q.tol > 0.0) || q.maxiter < 1 || q.maxiter > kMaxIter || !std::isfinite(q.kappa) ||
+            !std::isfinite(q.mu))
+            return fail(QCD_ERR_INVALID_ARG, "solve_cg: bad tol/maxiter/kappa/mu (system %d; maxiter in 1..%d)", k,
+                        kMaxIter);
         if (k > 0 && (q.maxiter != prm->maxiter || q.eo != prm->eo || q.normal != prm->normal ||
                       q.inner_prec != prm->inner_prec || q.inner_recon != prm->inner_recon ||
                       q.reliable_delta != prm->reliable_delta))
@@ -517,9 +595,10 @@ qcd_status qcd::solve_impl(const qcd_gauge *g, qcd_spinor *const *x, const qcd_s
     }
 
     // ---- right-hand side of the CG system
+    FieldView bp{};  // b'_e (eo)
     if (c.eo) {
         const FieldView be = half_of(bf, 0), bo = half_of(bf, 1);
-        const FieldView bp = ws_field(lat, "cg_bp", 1, QCD_PREC_F64, L);
+        bp = ws_field(lat, "cg_bp", 1, QCD_PREC_F64, L);
         if (!bp.hv[0].data) return fail(QCD_ERR_OOM, "solve_cg: workspace");
         const FieldView *src = &bo;
         if (tw) {  // th = A^-1 b_o
@@ -558,7 +637,20 @@ qcd_status qcd::solve_impl(const qcd_gauge *g, qcd_spinor *const *x, const qcd_s
     }
 
     // ---- CG
-    CgFields F{c, Uh, Us, g->recon, srecon, mixed, rhs, xh, rh, qh, th, sh, rs, ps, qs, ts, ss, xs, red, lat->state};
+    const bool split = mixed && (c.eo || !prm->normal);
+    const bool mid = split && (sp == QCD_PREC_F16 || sp == QCD_PREC_BF16);
+    GaugeView Um = Us;
+    FieldView rho_m{}, t_m{}, r_m{};
+    if (mid) {
+        Um = gauge_view(g, QCD_PREC_F32, srecon, s, &st);
+        if (st != QCD_OK) return st;
+        rho_m = ws_field(lat, "cg_rho32", nh, QCD_PREC_F32, L);
+        t_m = ws_field(lat, "cg_t32", 1, QCD_PREC_F32, L);
+        r_m = ws_field(lat, "cg_r32", nh, QCD_PREC_F32, L);
+        if (!rho_m.hv[0].data || !t_m.hv[0].data || !r_m.hv[0].data) return fail(QCD_ERR_OOM, "solve_cg: workspace");
+    }
+    CgFields F{c, Uh, Us, g->recon, srecon, mixed, rhs, xh, rh, qh, th, sh, rs, ps, qs, ts, ss, xs, red, lat->state,
+               split, c.eo ? bp : bf, Um, srecon, mid, rho_m, t_m, r_m};
     const double delta = mixed ? prm->reliable_delta : 0.0;
     RhsValues tol2{};
     for (int k = 0; k < kMaxRhs; ++k) tol2.v[k] = prm[k < nrhs ? k : 0].tol * prm[k < nrhs ? k : 0].tol;
@@ -581,7 +673,8 @@ qcd_status qcd::solve_impl(const qcd_gauge *g, qcd_spinor *const *x, const qcd_s
         // kernels the graph ran: per trip the iteration and two control
         // kernels, per reliable update its body
         const int op = c.eo ? 4 : 2;
-        note_launches(lat->state_host->trips * (op + 4) + lat->state_host->reliable_updates * (op + 2 + (mixed ? 1 : 0)));
+        const int per_update = split ? (c.eo ? 10 : 7) + (mid ? 1 : 0) : op + 2 + (mixed ? 1 : 0);
+        note_launches(lat->state_host->trips * (op + 4) + lat->state_host->reliable_updates * per_update);
     } else {
         QCD_TRY(cg_eager(lat, F, s), "solve_cg: iterations");
     }

@@ -21,7 +21,8 @@ LIB_PATH = os.path.join(_HERE, "libqcd.so")
 PREC = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3, "df64": 4}
 PARITY = {"even": 0, "odd": 1, "full": 2}
 STATUS = {0: "QCD_OK", 1: "QCD_ERR_INVALID_ARG", 2: "QCD_ERR_OOM", 3: "QCD_ERR_CUDA",
-          4: "QCD_ERR_NOT_CONVERGED", 5: "QCD_ERR_BREAKDOWN", 6: "QCD_ERR_TIMEOUT"}
+          4: "QCD_ERR_NOT_CONVERGED", 5: "QCD_ERR_BREAKDOWN", 6: "QCD_ERR_TIMEOUT",
+          7: "QCD_ERR_CANCELLED"}
 
 _p = ctypes.c_void_p
 _i = ctypes.c_int
@@ -89,6 +90,7 @@ _SIGS = {
     "qcd_profile_begin": (_i, []),
     "qcd_profile_end": (_i, [ctypes.POINTER(Profile)]),
     "qcd_kernel_launches": (ctypes.c_ulonglong, []),
+    "qcd_debug_inject": (_i, [_i, _i]),
     "qcd_norm2_noalloc": (_i, [_p, ctypes.c_size_t, _p, _p]),
     "qcd_server_create": (_i, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_p)]),
     "qcd_server_add_gauge": (_i, [_p, _p, ctypes.POINTER(_i)]),
@@ -399,6 +401,15 @@ def kernel_launches() -> int:
 
 
 NORM2_NOALLOC_MAX = 16_777_216
+
+
+INJECT_SPINOR_CREATE = 1
+
+
+def debug_inject(what: int, count: int):
+    """qcd_debug_inject: the next `count` calls of kind `what` fail with
+    QCD_ERR_OOM on the host (tests of error paths)."""
+    _check(lib().qcd_debug_inject(int(what), int(count)), "qcd_debug_inject")
 
 
 def norm2_noalloc(x_ptr: int, n: int, result_ptr: int, stream=None):

@@ -78,3 +78,10 @@ int main(void) {
     P, S = qcd.SolverParams, qcd.SolverStats
     assert [int(v) for v in out] == [ctypes.sizeof(P), P.reliable_delta.offset, P.inner_recon.offset,
                                      ctypes.sizeof(S), S.true_rel_residual.offset, S.seconds.offset]
+
+
+def test_debug_inject_rejects_unknown_kinds(qcd):
+    lib = qcd.lib()
+    assert lib.qcd_debug_inject(99, 1) == 1
+    assert lib.qcd_debug_inject(qcd.INJECT_SPINOR_CREATE, -1) == 1
+    assert lib.qcd_debug_inject(qcd.INJECT_SPINOR_CREATE, 0) == 0

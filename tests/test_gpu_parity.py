@@ -713,6 +713,65 @@ def test_server_same_alone_and_in_mix(q):
     sv.close()
 
 
+def test_server_recovers_from_a_failed_context_build(q):
+    """A solver context whose build fails part-way (its first spinor
+    allocation fails, injected on the host) is dropped whole: that request
+    ends with QCD_ERR_OOM, and the next request for the same volume on the
+    same slot builds the context again and solves."""
+    dims = (8, 8, 8, 4)
+    lat, U, g = _server_problem(q, dims, 321)
+    sv = q.Server(slots=1, memory_budget=4 << 30)
+    gid = sv.add_gauge(g)
+    b = syn.gaussian_spinor(dims, 5)
+    x = np.empty_like(b)
+    try:
+        for skip_b in (True, False):
+            # the lattice is built, then the spinor b (skip_b) or x fails
+            q.debug_inject(q.INJECT_SPINOR_CREATE, 1)
+            if not skip_b:
+                q.debug_inject(q.INJECT_SPINOR_CREATE, 0)
+            r = sv.wait(sv.submit(gid, b, x, 0.13, inner_prec="f16"))
+            if skip_b:
+                assert r["status"] == 2, r
+            r = sv.wait(sv.submit(gid, b, x, 0.13, inner_prec="f16"))
+            assert r["status"] == 0 and r["stats"]["true_rel_residual"] <= 1e-10, r
+        assert schur_residual_oracle(U, b, x, 0.13, 0.0) <= 1.5e-10
+    finally:
+        q.debug_inject(q.INJECT_SPINOR_CREATE, 0)
+        sv.close()
+
+
+def test_server_destroy_cancels_queued_requests(q):
+    """Destroying a server with requests still queued: threads blocked in
+    wait() on queued requests return QCD_ERR_CANCELLED, the running request
+    finishes, and destroy returns only after the waiters have left."""
+    import threading
+    import time
+    dims = (32, 32, 32, 8)
+    lat, U, g = _server_problem(q, dims, 322)
+    sv = q.Server(slots=1, memory_budget=16 << 30)
+    gid = sv.add_gauge(g)
+    bs = [syn.gaussian_spinor(dims, 10 + k) for k in range(6)]
+    xs = [np.empty_like(b) for b in bs]
+    # FP64 solves of ~30 ms each on one slot: while the first runs, the rest queue
+    ids = [sv.submit(gid, b, x, 0.16, tol=1e-12, inner_prec="f64") for b, x in zip(bs, xs)]
+    out = {}
+
+    def waiter(k):
+        out[k] = sv.wait(ids[k])
+
+    ths = [threading.Thread(target=waiter, args=(k,)) for k in range(len(ids))]
+    for t in ths:
+        t.start()
+    time.sleep(0.01)  # the waiters block inside wait()
+    sv.close()
+    for t in ths:
+        t.join(timeout=60)
+        assert not t.is_alive()
+    st = [out[k]["status"] for k in range(len(ids))]
+    assert st[0] == 0 and all(v in (0, 7) for v in st) and 7 in st, st
+
+
 def test_server_concurrent_first_use_of_a_precision(q):
     """Requests on a gauge field with no prepared copies, running at the same
     time on several slots: the copies they need (FP16 links, FP32 links for

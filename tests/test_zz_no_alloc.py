@@ -60,3 +60,29 @@ def test_norm2_noalloc_edges(q):
     with pytest.raises(q.QcdError) as e:
         q.norm2_noalloc(x.data_ptr(), q.NORM2_NOALLOC_MAX + 1, res.data_ptr())
     assert e.value.status == 1 and "exceeds the maximum" in str(e.value)
+
+
+def test_norm2_noalloc_at_the_limit_and_block_edges(q):
+    """The largest accepted size (every partial-sum slot in use, the ticket
+    counter right after the last one) and sizes one element either side of a
+    block boundary, against a sum of squares in FP64 on the device; around
+    repeated calls the free device memory does not change."""
+    import torch
+    per_block = 256 * 8
+    res = torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
+    n_max = q.NORM2_NOALLOC_MAX
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(99)
+    x = torch.rand(n_max, dtype=torch.float64, device="cuda", generator=gen) - 0.5
+    sizes = (n_max, n_max - 1, 3 * per_block - 1, 3 * per_block, 3 * per_block + 1, 1)
+    wants = [float(torch.dot(x[:n], x[:n]).item()) for n in sizes]
+    q.norm2_noalloc(x.data_ptr(), n_max, res.data_ptr())  # first use of the entry point (module set-up)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for n, want in zip(sizes, wants):
+        for _ in range(2):
+            q.norm2_noalloc(x.data_ptr(), n, res.data_ptr())
+            q.stream_sync()
+            assert abs(res.item() - want) <= 1e-12 * want, n
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
