@@ -383,17 +383,17 @@ def batched_block(qcd, torch, flush, hbm, reps):
     return res
 
 
-def serving_block(qcd, torch, n_requests=2000, rate=30.0, slots=8, seed=1006):
+def serving_block(qcd, torch, n_requests=2000, rate=30.0, slots=8, seed=1006, vols=None, batch_small_sites=0):
     """Serving: a Poisson stream of even-odd solves of five volumes, kappa
     uniform in [0.12, 0.16], 3 resident gauge fields per volume, FP16-mixed
     CG to 1e-10, admitted by slot and device-memory budget."""
     import threading
     from paper_1411_5219_gb300 import synthetic as syn
     rng = np.random.default_rng(seed)
-    vols = syn.SWEEP_VOLUMES
+    vols = syn.SWEEP_VOLUMES if vols is None else vols
     t_setup = time.time()
     fields, gids, pools = [], {}, {}
-    sv = qcd.Server(slots=slots, memory_budget=64 << 30)
+    sv = qcd.Server(slots=slots, memory_budget=64 << 30, batch_small_sites=batch_small_sites)
     for vi, dims in enumerate(vols):
         lat = qcd.Lattice(dims, -1)
         for k in range(3):
@@ -444,6 +444,7 @@ def serving_block(qcd, torch, n_requests=2000, rate=30.0, slots=8, seed=1006):
         d = per_vol.setdefault("x".join(map(str, vols[vi])), [])
         d.append(r["t_end"] - r["t_start"])
     out = {"requests": n_requests, "arrival_rate_per_s": rate, "slots": slots, "memory_budget_GiB": 64,
+           "batch_small_sites": batch_small_sites,
            "solves_s": n_requests / span, "wall_s": wall, "setup_s": t_setup,
            "latency_p50_ms": float(np.percentile(lat_s, 50) * 1e3),
            "latency_p99_ms": float(np.percentile(lat_s, 99) * 1e3),
@@ -461,6 +462,50 @@ def serving_block(qcd, torch, n_requests=2000, rate=30.0, slots=8, seed=1006):
         out["failures"] = bad[:10]
     sv.close()
     return out
+
+
+def many_block(qcd, torch, flush, reps=5):
+    """Uneven small volumes in one persistent launch (qcd_solve_cg_many): 16
+    systems -- 8 of 8^3x4, 4 of 12^3x4, 4 of 4^4 -- each with its own gauge
+    field, kappa (0.12 .. 0.15) and mu (0 or 0.01), FP64 CG to 1e-10, against
+    the same 16 solved one by one with the FP64 graph solver and with the
+    FP16-mixed one."""
+    from paper_1411_5219_gb300 import synthetic as syn
+    vols = [(8, 8, 8, 4)] * 8 + [(12, 12, 12, 4)] * 4 + [(4, 4, 4, 4)] * 4
+    systems = []
+    for k, dims in enumerate(vols):
+        lat = qcd.Lattice(dims, -1)
+        g = qcd.Gauge(lat, "f64", 18)
+        g.upload(syn.gauge_field(dims, 0.2, 1100 + k))
+        g.prepare("f16", 12)
+        b = qcd.Spinor(lat, "full", "f64")
+        b.upload(syn.gaussian_spinor(dims, 1200 + k))
+        x = qcd.Spinor(lat, "full", "f64")
+        systems.append((lat, g, b, x, 0.12 + 0.002 * k, 0.01 * (k % 2)))
+    gs, bs, xs = [s_[1] for s_ in systems], [s_[2] for s_ in systems], [s_[3] for s_ in systems]
+    kap, mus = [s_[4] for s_ in systems], [s_[5] for s_ in systems]
+    n = len(systems)
+    for _ in range(2):
+        qcd.solve_cg_many(gs, xs, bs, kap, mus)
+    st_many = []
+    tm = timed_steps(torch, lambda: st_many.append(qcd.solve_cg_many(gs, xs, bs, kap, mus)[1]), reps, flush)
+
+    def seq(inner):
+        for g, b, x, k_, m_ in zip(gs, bs, xs, kap, mus):
+            qcd.solve_cg(g, x, b, k_, m_, inner_prec=inner)
+
+    seq("f64")
+    seq("f16")
+    t64 = timed_steps(torch, lambda: seq("f64"), max(2, reps // 2), flush)
+    t16 = timed_steps(torch, lambda: seq("f16"), max(2, reps // 2), flush)
+    v_many = n * reps / float(np.sum(tm))
+    v64 = n * max(2, reps // 2) / float(np.sum(t64))
+    v16 = n * max(2, reps // 2) / float(np.sum(t16))
+    return {"systems": n, "volumes": "8 x 8^3x4, 4 x 12^3x4, 4 x 4^4", "many_solves_s": v_many,
+            "sequential_fp64_solves_s": v64, "sequential_f16_mixed_solves_s": v16,
+            "speedup_vs_fp64": v_many / v64, "speedup_vs_mixed": v_many / v16,
+            "ms_per_launch": float(np.mean(tm)) * 1e3,
+            "max_true_rel_residual": max(s_["true_rel_residual"] for s_ in st_many[-1])}
 
 
 def dslash_ks_sweep(qcd, torch, flush, hbm, reps=20):
@@ -802,6 +847,7 @@ def main():
         t4 = timed_steps(torch, lambda: p4.solve(qcd, eo=False, normal=True), args.steps, flush)
         line["full_4x4_normal_solves_s"] = args.steps / float(np.sum(t4))
         del p4
+        many = many_block(qcd, torch, flush)
         serving = serving_block(qcd, torch, n_requests=args.serve_requests)
         line["dslash_ks_sweep"] = dslash_ks_sweep(qcd, torch, flush, hbm)
         host_fields = {}
@@ -827,8 +873,10 @@ def main():
         line["mixed_vs_fp64_detail"] = mixed
         line["batched_multi_rhs_detail"] = batched
         line["serving_detail"] = serving
+        line["many_systems_detail"] = many
         line["dslash_48x48x48x12_frac_hbm"] = {k: v["frac_hbm"] for k, v in line["dslash_sweep"]["48x48x48x12"].items()
                                                if k in ("f32_r12", "f16_r12", "bf16_r12")}
+        line["many_systems"] = {k: _sig(many[k], 3) for k in ("many_solves_s", "speedup_vs_fp64", "speedup_vs_mixed")}
         line["batched_multi_rhs"] = batched_summary(batched)
         line["serving"] = serving_summary(serving)
         line["mixed_vs_fp64"] = mixed_summary(mixed)

@@ -297,6 +297,61 @@ qcd_status qcd_solve_cg_multi(const qcd_gauge *g, qcd_spinor *const *x, const qc
 qcd_status qcd_solve_cg_batch(const qcd_gauge *g, qcd_spinor *const *x, const qcd_spinor *const *b, int n,
                               const qcd_solver_params *params, qcd_solver_stats *stats, void *stream);
 
+/* n (1..32) independent even-odd FP64 CG solves -- each with its own gauge
+ * field, lattice volume, hopping parameter, twisted mass and tolerance --
+ * advanced together by ONE persistent cooperative kernel launch (source
+ * preparation, CG, FP64 true-residual check, odd-site reconstruction and the
+ * full-system residual, separated by grid-wide barriers instead of kernel
+ * launches).  Meant for small lattices, where one solve cannot fill the GPU:
+ * the paper's finite-temperature studies are many independent runs over
+ * couplings and volumes (Sec. 1) within device memory (Sec. 2).
+ * gauges[k]: F64 field; x[k], b[k]: FULL F64 spinors on one lattice with the
+ * gauge field's extents -- its own lattice or another handle (a context
+ * lattice, which then holds the scratch, so that calls on different context
+ * lattices may run concurrently on the same gauge field); distinct x;
+ * params[k].eo = 1, normal = 0, inner_prec = F64, one maxiter for all.
+ * Blocks are shared out in proportion to the site counts, so each result is
+ * bitwise the same alone and in any batch.  wait_cycles bounds every
+ * barrier wait (0: about two seconds); when a wait runs out the call
+ * returns QCD_ERR_TIMEOUT and the context stays usable.  The systems' lattice
+ * handles hold the scratch fields, so calls that share a lattice must not
+ * overlap on the device.  Synchronous (returns after the stats are final);
+ * errors as for qcd_solve_cg, per system in stats. */
+qcd_status qcd_solve_cg_many(int n, const qcd_gauge *const *gauges, qcd_spinor *const *x, const qcd_spinor *const *b,
+                             const qcd_solver_params *params, qcd_solver_stats *stats, long long wait_cycles,
+                             void *stream);
+
+/* ---------------------------------------------------- time-slab split
+ * The paper splits the lattice in the time direction across devices
+ * (Sec. 7).  A rank holding Lt_loc consecutive time slices (Lt_loc even, so
+ * even-odd parities agree with the global ones up to one swap) works on an
+ * EXTENDED lattice of Lt_loc + 2 slices created with t_bc = +1: slices
+ * 1 .. Lt_loc are its own, slices 0 and Lt_loc + 1 are halos.  Its gauge
+ * field holds the rank's links on the own slices and identity links on the
+ * halo slices.  Before each hopping-term application on a half field `in`:
+ *   qcd_face_pack(TO_PREV): h = psi_up - S psi_dn of own slice 1 (S = +1 for
+ *     D, -1 for D^dagger), for the previous rank's forward t hops;
+ *   qcd_face_pack(TO_NEXT): u = U_t(x)^dagger (psi_up + S psi_dn) of the last
+ *     own slice, for the next rank's backward t hops;
+ *   `sign` multiplies the face: t_bc where the face crosses the global time
+ *   boundary (the previous rank of rank 0 is the last rank), else 1;
+ *   the faces are exchanged by the caller into the receiver's own device
+ *   buffers, and qcd_face_unpack(FROM_NEXT / FROM_PREV) writes them into
+ *   the halo slices (upper spins = face, lower spins = 0);
+ *   qcd_apply_dslash on the extended lattice then gives D_eo (or D_eo^dag)
+ *   on the own slices.  Faces are 6 complex per site of one parity in one
+ *   time slice: face_dev holds 6 * (Lx Ly Lz / 2) double2, component-major.
+ * F64 fields and gauge only; INVALID_ARG for other fields or a lattice that
+ * is not an extended slab (t_bc = +1, >= 4 slices).  Asynchronous on
+ * `stream`. */
+#define QCD_FACE_TO_PREV 0
+#define QCD_FACE_TO_NEXT 1
+#define QCD_FACE_FROM_PREV 2
+#define QCD_FACE_FROM_NEXT 3
+qcd_status qcd_face_pack(const qcd_gauge *g, const qcd_spinor *in, int face, int dagger, double sign, double *face_dev,
+                         void *stream);
+qcd_status qcd_face_unpack(qcd_spinor *out, int face, const double *face_dev, void *stream);
+
 /* ----------------------------------------------------------------- server */
 
 /* A solve server: independent even-odd CG solves of different volumes and
@@ -314,6 +369,11 @@ typedef struct qcd_server qcd_server;
 typedef struct {
     int slots;             /* concurrent solves (1..64) */
     size_t memory_budget;  /* device bytes the solver contexts may use */
+    int batch_small_sites; /* 0: off; else requests on lattices of at most this
+                              many sites that are queued together (up to 16,
+                              same maxiter) run as one qcd_solve_cg_many launch
+                              (FP64 CG, which is faster than a mixed solve at
+                              such volumes; the same 1e-10-type target) */
 } qcd_server_config;
 typedef struct {
     int gauge_id;          /* from qcd_server_add_gauge */

@@ -14,6 +14,8 @@
 namespace qcd {
 
 static thread_local char g_err[512] = "";
+// set by lattice_create_on for the duration of one qcd_lattice_create call
+static thread_local cudaStream_t g_create_stream = nullptr;
 static std::atomic<unsigned long long> g_launches{0};
 
 std::shared_mutex &device_mutex()
@@ -167,12 +169,86 @@ static qcd_status check_recon8(const GaugeView &dst, int prec, const double2 *ao
     return QCD_OK;
 }
 
+// ----------------------------------------------------------------- memory
+
+// Device memory of a lattice's buffers: stream-ordered on lat->alloc_stream
+// when it is set (no device-wide synchronisation), else cudaMalloc/cudaFree.
+static cudaError_t lat_alloc(const qcd_lattice *lat, void **p, size_t n)
+{
+    return lat && lat->alloc_stream ? cudaMallocAsync(p, n, lat->alloc_stream) : cudaMalloc(p, n);
+}
+static void lat_free(const qcd_lattice *lat, void *p)
+{
+    if (!p) return;
+    if (lat && lat->alloc_stream)
+        cudaFreeAsync(p, lat->alloc_stream);
+    else
+        cudaFree(p);
+}
+cudaError_t zero_now(void *p, size_t n);
+static cudaError_t lat_zero(const qcd_lattice *lat, void *p, size_t n)
+{
+    return lat && lat->alloc_stream ? cudaMemsetAsync(p, 0, n, lat->alloc_stream) : zero_now(p, n);
+}
+
+// Pinned staging buffers (CG state mirror, coefficient table) of
+// stream-ordered lattices are reused instead of freed: cudaFreeHost may
+// synchronise the device.
+static std::mutex g_pinned_mu;
+static std::vector<std::pair<void *, void *>> g_pinned_pool;
+
+static cudaError_t pinned_get(void **state, void **coef)
+{
+    {
+        std::lock_guard<std::mutex> lk(g_pinned_mu);
+        if (!g_pinned_pool.empty()) {
+            *state = g_pinned_pool.back().first;
+            *coef = g_pinned_pool.back().second;
+            g_pinned_pool.pop_back();
+            return cudaSuccess;
+        }
+    }
+    cudaError_t e = cudaMallocHost(state, sizeof(CgState));
+    if (e == cudaSuccess) e = cudaMallocHost(coef, kCoefHostDoubles * sizeof(double));
+    return e;
+}
+static void pinned_put(void *state, void *coef)
+{
+    if (!state || !coef) {
+        if (state) cudaFreeHost(state);
+        if (coef) cudaFreeHost(coef);
+        return;
+    }
+    std::lock_guard<std::mutex> lk(g_pinned_mu);
+    g_pinned_pool.emplace_back(state, coef);
+}
+
 // ----------------------------------------------------------------- views
 
 void *workspace(const qcd_lattice *lat, const std::string &name, size_t bytes)
 {
     auto it = lat->ws.find(name);
     if (it != lat->ws.end() && it->second.second >= bytes) return it->second.first;
+    if (lat->alloc_stream) {
+        // stream-ordered: only this lattice's own stream is waited for
+        if (it != lat->ws.end()) {
+            cudaStreamSynchronize(lat->alloc_stream);
+            for (auto &kv : lat->graphs) {
+                cudaGraphExecDestroy(kv.second.exec);
+                cudaGraphDestroy(kv.second.graph);
+            }
+            lat->graphs.clear();
+            lat_free(lat, it->second.first);
+            lat->ws.erase(it);
+        }
+        void *p = nullptr;
+        if (lat_alloc(lat, &p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        lat->ws[name] = {p, bytes};
+        return p;
+    }
     DeviceLock dl(device_mutex());
     if (it != lat->ws.end()) {
         // cached CG graphs may hold this buffer's address: drop them all
@@ -539,6 +615,14 @@ cudaError_t hop(const qcd_lattice *lat, const GaugeView &U, int recon, const Hop
 
 using namespace qcd;
 
+qcd_status qcd::lattice_create_on(const int dims[4], int t_bc, cudaStream_t s, qcd_lattice **out)
+{
+    g_create_stream = s;
+    const qcd_status st = qcd_lattice_create(dims, t_bc, out);
+    g_create_stream = nullptr;
+    return st;
+}
+
 // =================================================================== C ABI
 
 extern "C" {
@@ -630,7 +714,9 @@ qcd_status qcd_lattice_create(const int dims[4], int t_bc, qcd_lattice **out)
         return fail(QCD_ERR_INVALID_ARG, "lattice_create: volume too large");
     qcd_lattice *lat = new (std::nothrow) qcd_lattice();
     if (!lat) return fail(QCD_ERR_OOM, "lattice_create: host allocation");
-    DeviceLock dl(device_mutex());
+    lat->alloc_stream = g_create_stream;
+    DeviceLock dl(device_mutex(), std::defer_lock);
+    if (!lat->alloc_stream) dl.lock();
     memcpy(lat->dims, dims, sizeof(lat->dims));
     lat->t_bc = t_bc;
     cudaGetDevice(&lat->device);
@@ -649,18 +735,22 @@ qcd_status qcd_lattice_create(const int dims[4], int t_bc, qcd_lattice **out)
     lat->stride = (int)((h + 63) / 64 * 64);
     // partials of the largest grid: 64-thread blocks over all V sites
     lat->red_cap = 2 * (((size_t)V + 63) / 64 + 64);
-    cudaError_t e = cudaMalloc(&lat->red_partials, lat->red_cap * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&lat->red_counter, 64);
-    if (e == cudaSuccess) e = cudaMalloc(&lat->red_out, 8 * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&lat->red_out_big, 2 * kMaxRhs * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&lat->state, sizeof(CgState));
-    if (e == cudaSuccess) e = cudaMallocHost(&lat->state_host, sizeof(CgState));
-    if (e == cudaSuccess) e = cudaMallocHost(&lat->coef_host, kCoefHostDoubles * sizeof(double));
-    if (e == cudaSuccess) e = zero_now(lat->red_counter, 64);
-    if (e == cudaSuccess) e = zero_now(lat->state, sizeof(CgState));
+    cudaError_t e = lat_alloc(lat, (void **)&lat->red_partials, lat->red_cap * sizeof(double));
+    if (e == cudaSuccess) e = lat_alloc(lat, (void **)&lat->red_counter, 64);
+    if (e == cudaSuccess) e = lat_alloc(lat, (void **)&lat->red_out, 8 * sizeof(double));
+    if (e == cudaSuccess) e = lat_alloc(lat, (void **)&lat->red_out_big, 2 * kMaxRhs * sizeof(double));
+    if (e == cudaSuccess) e = lat_alloc(lat, (void **)&lat->state, sizeof(CgState));
+    if (lat->alloc_stream) {
+        if (e == cudaSuccess) e = pinned_get((void **)&lat->state_host, (void **)&lat->coef_host);
+    } else {
+        if (e == cudaSuccess) e = cudaMallocHost(&lat->state_host, sizeof(CgState));
+        if (e == cudaSuccess) e = cudaMallocHost(&lat->coef_host, kCoefHostDoubles * sizeof(double));
+    }
+    if (e == cudaSuccess) e = lat_zero(lat, lat->red_counter, 64);
+    if (e == cudaSuccess) e = lat_zero(lat, lat->state, sizeof(CgState));
     if (e != cudaSuccess) {
         qcd_status st = check_cuda(e, "lattice_create");
-        dl.unlock();
+        if (dl.owns_lock()) dl.unlock();
         qcd_lattice_destroy(lat);
         return st;
     }
@@ -671,6 +761,23 @@ qcd_status qcd_lattice_create(const int dims[4], int t_bc, qcd_lattice **out)
 void qcd_lattice_destroy(qcd_lattice *lat)
 {
     if (!lat) return;
+    if (lat->alloc_stream) {
+        // stream-ordered: wait for this lattice's own stream only (its graphs
+        // and staging must be idle), then free in stream order
+        cudaStreamSynchronize(lat->alloc_stream);
+        for (auto &kv : lat->graphs) {
+            cudaGraphExecDestroy(kv.second.exec);
+            cudaGraphDestroy(kv.second.graph);
+        }
+        for (void *p : {(void *)lat->red_partials, (void *)lat->red_counter, (void *)lat->red_out,
+                        (void *)lat->red_out_big, (void *)lat->state})
+            lat_free(lat, p);
+        for (auto &kv : lat->ws) lat_free(lat, kv.second.first);
+        pinned_put(lat->state_host, lat->coef_host);
+        if (lat->capture_stream) cudaStreamDestroy(lat->capture_stream);
+        delete lat;
+        return;
+    }
     DeviceLock dl(device_mutex());
     cudaDeviceSynchronize();
     cudaFree(lat->red_partials);
@@ -801,15 +908,16 @@ qcd_status qcd_spinor_create(const qcd_lattice *lat, qcd_parity parity, qcd_prec
     qcd_spinor *s = new_spinor(lat, parity, prec);
     if (!s) return fail(QCD_ERR_OOM, "spinor_create: host allocation");
     const int nh = parity == QCD_PARITY_FULL ? 2 : 1;
-    DeviceLock dl(device_mutex());
-    cudaError_t e = cudaMalloc(&s->data, nh * s->half_data_bytes);
-    if (e == cudaSuccess && s->half_norm_bytes) e = cudaMalloc(reinterpret_cast<void **>(&s->norm), nh * s->half_norm_bytes);
-    if (e == cudaSuccess) e = zero_now(s->data, nh * s->half_data_bytes);
-    if (e == cudaSuccess && s->norm) e = zero_now(s->norm, nh * s->half_norm_bytes);
+    DeviceLock dl(device_mutex(), std::defer_lock);
+    if (!lat->alloc_stream) dl.lock();
+    cudaError_t e = lat_alloc(lat, &s->data, nh * s->half_data_bytes);
+    if (e == cudaSuccess && s->half_norm_bytes) e = lat_alloc(lat, reinterpret_cast<void **>(&s->norm), nh * s->half_norm_bytes);
+    if (e == cudaSuccess) e = lat_zero(lat, s->data, nh * s->half_data_bytes);
+    if (e == cudaSuccess && s->norm) e = lat_zero(lat, s->norm, nh * s->half_norm_bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        cudaFree(s->data);
-        cudaFree(s->norm);
+        lat_free(lat, s->data);
+        lat_free(lat, s->norm);
         delete s;
         return fail(QCD_ERR_OOM, "spinor_create: cudaMalloc failed");
     }
@@ -903,7 +1011,11 @@ qcd_status qcd_spinor_wrap_device(const qcd_lattice *lat, qcd_parity parity, qcd
 void qcd_spinor_destroy(qcd_spinor *s)
 {
     if (!s) return;
-    if (s->owns) {
+    if (s->owns && s->lat->alloc_stream) {
+        // stream-ordered lattice: freed after the work queued on its stream
+        lat_free(s->lat, s->data);
+        lat_free(s->lat, s->norm);
+    } else if (s->owns) {
         DeviceLock dl(device_mutex());
         cudaDeviceSynchronize();
         cudaFree(s->data);

@@ -40,6 +40,13 @@ struct qcd_lattice {
     mutable std::map<std::string, GraphEntry> graphs;
     mutable unsigned long long graph_clock = 0;
     mutable cudaStream_t capture_stream = nullptr;
+    // Stream-ordered memory (set for the solve server's contexts): device
+    // buffers of this lattice, its workspace and its spinors are allocated
+    // with cudaMallocAsync and freed with cudaFreeAsync on this stream, and
+    // the pinned staging comes from a reuse pool, so creating, growing and
+    // destroying them never synchronises the whole device.  Every use must
+    // then be ordered after `alloc_stream` (the server uses this stream only).
+    cudaStream_t alloc_stream = nullptr;
 };
 
 struct qcd_gauge {
@@ -88,6 +95,10 @@ size_t gauge_bytes(int prec, int recon, int stride);
 
 // Workspace buffer `name` of at least `bytes` on the lattice.
 void *workspace(const qcd_lattice *lat, const std::string &name, size_t bytes);
+
+// A lattice (and, through qcd_spinor_create on it, its spinors) whose device
+// memory is stream-ordered on `s` (see qcd_lattice::alloc_stream).
+qcd_status lattice_create_on(const int dims[4], int t_bc, cudaStream_t s, qcd_lattice **out);
 
 // Views.
 FieldView view_of(const qcd_spinor *s);

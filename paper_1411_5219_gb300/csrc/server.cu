@@ -35,6 +35,7 @@ using clock_type = std::chrono::steady_clock;
 struct VolumeCtx {
     qcd_lattice *lat = nullptr;
     qcd_spinor *b = nullptr, *x = nullptr;
+    std::vector<std::pair<qcd_spinor *, qcd_spinor *>> more;  // b, x of further systems of a batch
     size_t reserved = 0;  // bytes counted against the budget
 };
 
@@ -68,6 +69,7 @@ struct qcd_server {
     int device = 0;
     size_t budget = 0, used = 0;
     int nslots = 0;
+    int batch_small = 0;  // sites at most, for batching small requests (0: off)
     clock_type::time_point t0;
     std::vector<const qcd_gauge *> gauges;
     std::deque<Job *> queue;
@@ -90,6 +92,10 @@ namespace {
 
 void release(qcd_server *sv, VolumeCtx &c)
 {
+    for (auto &bx : c.more) {
+        qcd_spinor_destroy(bx.first);
+        qcd_spinor_destroy(bx.second);
+    }
     qcd_spinor_destroy(c.b);
     qcd_spinor_destroy(c.x);
     qcd_lattice_destroy(c.lat);
@@ -126,6 +132,11 @@ void run_job(qcd_server *sv, int s, Job *j)
         c = &sv->slot_ctx[s][dims_key(g->lat)];
     }
     qcd_status st = QCD_OK;
+    // Small volumes run on the slot's high-priority stream, so their few
+    // short kernels are not queued behind the long ones of large volumes.
+    // The context's device memory is stream-ordered on that stream: building
+    // or releasing a context never synchronises the other slots' work.
+    cudaStream_t stream = (size_t)g->lat->h * 2 <= kSmallVolume ? sv->streams[s] : sv->streams_lo[s];
     if (!c->lat || !c->b || !c->x) {
         // build the context whole; a part left by an earlier failed build is
         // dropped first, and a failed build leaves nothing behind (the
@@ -135,7 +146,7 @@ void run_job(qcd_server *sv, int s, Job *j)
         qcd_lattice_destroy(c->lat);
         c->lat = nullptr;
         c->b = c->x = nullptr;
-        st = qcd_lattice_create(g->lat->dims, g->lat->t_bc, &c->lat);
+        st = qcd::lattice_create_on(g->lat->dims, g->lat->t_bc, stream, &c->lat);
         if (st == QCD_OK) st = qcd_spinor_create(c->lat, QCD_PARITY_FULL, QCD_PREC_F64, &c->b);
         if (st == QCD_OK) st = qcd_spinor_create(c->lat, QCD_PARITY_FULL, QCD_PREC_F64, &c->x);
         if (st != QCD_OK) {
@@ -146,9 +157,6 @@ void run_job(qcd_server *sv, int s, Job *j)
             c->b = c->x = nullptr;
         }
     }
-    // Small volumes run on the slot's high-priority stream, so their few
-    // short kernels are not queued behind the long ones of large volumes.
-    cudaStream_t stream = (size_t)g->lat->h * 2 <= kSmallVolume ? sv->streams[s] : sv->streams_lo[s];
     if (st == QCD_OK) st = qcd_spinor_upload(c->b, j->req.b_host, stream);
     if (st == QCD_OK) {
         const qcd_request &r = j->req;
@@ -166,6 +174,90 @@ void run_job(qcd_server *sv, int s, Job *j)
     j->status = st;
 }
 
+// Small requests taken together: one persistent launch solves them all
+// (qcd_solve_cg_many); each keeps its own b and x on its volume's context.
+void run_batch(qcd_server *sv, int s, std::vector<Job *> &jobs)
+{
+    cudaSetDevice(sv->device);
+    const int n = (int)jobs.size();
+    cudaStream_t stream = sv->streams[s];
+    std::vector<const qcd_gauge *> g(n);
+    std::vector<qcd_spinor *> xs(n);
+    std::vector<const qcd_spinor *> bs(n);
+    std::vector<qcd_solver_params> prm(n);
+    std::map<std::string, int> used;  // systems per volume so far
+    qcd_status st = QCD_OK;
+    for (int k = 0; k < n && st == QCD_OK; ++k) {
+        Job *j = jobs[k];
+        g[k] = sv->gauges[j->req.gauge_id];
+        VolumeCtx *c;
+        const std::string key = dims_key(g[k]->lat);
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            c = &sv->slot_ctx[s][key];
+        }
+        if (!c->lat || !c->b || !c->x) {
+            for (auto &bx : c->more) {
+                qcd_spinor_destroy(bx.first);
+                qcd_spinor_destroy(bx.second);
+            }
+            c->more.clear();
+            qcd_spinor_destroy(c->b);
+            qcd_spinor_destroy(c->x);
+            qcd_lattice_destroy(c->lat);
+            c->lat = nullptr;
+            c->b = c->x = nullptr;
+            st = qcd::lattice_create_on(g[k]->lat->dims, g[k]->lat->t_bc, stream, &c->lat);
+            if (st == QCD_OK) st = qcd_spinor_create(c->lat, QCD_PARITY_FULL, QCD_PREC_F64, &c->b);
+            if (st == QCD_OK) st = qcd_spinor_create(c->lat, QCD_PARITY_FULL, QCD_PREC_F64, &c->x);
+            if (st != QCD_OK) break;
+        }
+        const int o = used[key]++;
+        if (o == 0) {
+            bs[k] = c->b;
+            xs[k] = c->x;
+        } else {
+            while ((int)c->more.size() < o) {
+                qcd_spinor *b2 = nullptr, *x2 = nullptr;
+                st = qcd_spinor_create(c->lat, QCD_PARITY_FULL, QCD_PREC_F64, &b2);
+                if (st == QCD_OK) st = qcd_spinor_create(c->lat, QCD_PARITY_FULL, QCD_PREC_F64, &x2);
+                if (st != QCD_OK) {
+                    qcd_spinor_destroy(b2);
+                    qcd_spinor_destroy(x2);
+                    break;
+                }
+                c->more.emplace_back(b2, x2);
+            }
+            if (st != QCD_OK) break;
+            bs[k] = c->more[o - 1].first;
+            xs[k] = c->more[o - 1].second;
+        }
+        st = qcd_spinor_upload(const_cast<qcd_spinor *>(bs[k]), j->req.b_host, stream);
+        const qcd_request &r = j->req;
+        prm[k] = qcd_solver_params{r.kappa, r.mu, r.tol, r.maxiter, 1, 0, (qcd_prec)QCD_PREC_F64, (qcd_recon)18, r.reliable_delta};
+    }
+    std::vector<qcd_solver_stats> stats(n);
+    if (st == QCD_OK) st = qcd_solve_cg_many(n, g.data(), xs.data(), bs.data(), prm.data(), stats.data(), 0, stream);
+    const bool ran = st == QCD_OK || st == QCD_ERR_NOT_CONVERGED || st == QCD_ERR_BREAKDOWN;
+    qcd_status st2 = QCD_OK;
+    if (ran)
+        for (int k = 0; k < n && st2 == QCD_OK; ++k) st2 = qcd_spinor_download(xs[k], jobs[k]->req.x_host, stream);
+    if (st2 == QCD_OK) st2 = qcd_stream_sync(stream);
+    for (int k = 0; k < n; ++k) {
+        Job *j = jobs[k];
+        j->stats = stats[k];
+        if (!ran || st2 != QCD_OK)
+            j->status = st2 != QCD_OK ? st2 : st;
+        else  // per system: converged to its own target, else the batch's error
+            j->status = st == QCD_OK || stats[k].true_rel_residual <= j->req.tol ? QCD_OK : st;
+    }
+}
+
+bool small_job(const qcd_server *sv, const Job *j)
+{
+    return sv->batch_small > 0 && (long long)sv->gauges[j->req.gauge_id]->lat->h * 2 <= sv->batch_small;
+}
+
 void worker(qcd_server *sv, int s)
 {
     cudaSetDevice(sv->device);
@@ -180,13 +272,37 @@ void worker(qcd_server *sv, int s)
         }
         sv->queue.pop_front();
         sv->busy[s] = 1;
-        j->slot = s;
-        j->t_start = sv->now();
+        std::vector<Job *> batch{j};
+        if (small_job(sv, j)) {
+            // further small requests queued behind it, in order, while their
+            // contexts fit (same maxiter: one launch iterates them together)
+            for (auto it = sv->queue.begin(); it != sv->queue.end() && batch.size() < 16;) {
+                Job *c = *it;
+                if (!small_job(sv, c) || c->req.maxiter != j->req.maxiter) {
+                    ++it;
+                    continue;
+                }
+                if (!admit(sv, s, c)) break;
+                batch.push_back(c);
+                it = sv->queue.erase(it);
+            }
+        }
+        const double t = sv->now();
+        for (Job *b : batch) {
+            b->slot = s;
+            b->t_start = t;
+        }
         lk.unlock();
-        run_job(sv, s, j);
+        if (batch.size() == 1 && !small_job(sv, j))
+            run_job(sv, s, j);
+        else
+            run_batch(sv, s, batch);
         lk.lock();
-        j->t_end = sv->now();
-        j->done = true;
+        const double te = sv->now();
+        for (Job *b : batch) {
+            b->t_end = te;
+            b->done = true;
+        }
         sv->busy[s] = 0;
         sv->cv_done.notify_all();
         sv->cv_work.notify_all();
@@ -210,6 +326,7 @@ qcd_status qcd_server_create(const qcd_server_config *cfg, qcd_server **out)
     cudaGetDevice(&sv->device);
     sv->budget = cfg->memory_budget;
     sv->nslots = cfg->slots;
+    sv->batch_small = cfg->batch_small_sites > 0 ? cfg->batch_small_sites : 0;
     sv->t0 = clock_type::now();
     sv->slot_ctx.resize(cfg->slots);
     sv->busy.assign(cfg->slots, 0);

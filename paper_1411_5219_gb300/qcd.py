@@ -48,7 +48,7 @@ class Profile(ctypes.Structure):
 
 
 class ServerConfig(ctypes.Structure):
-    _fields_ = [("slots", _i), ("memory_budget", ctypes.c_size_t)]
+    _fields_ = [("slots", _i), ("memory_budget", ctypes.c_size_t), ("batch_small_sites", _i)]
 
 
 class Request(ctypes.Structure):
@@ -101,6 +101,10 @@ _SIGS = {
     "qcd_apply_dslash_multi": (_i, [_p, ctypes.POINTER(_p), ctypes.POINTER(_p), _i, _i, _p]),
     "qcd_solve_cg_multi": (_i, [_p, ctypes.POINTER(_p), ctypes.POINTER(_p), _i, ctypes.POINTER(SolverParams),
                                 ctypes.POINTER(SolverStats), _p]),
+    "qcd_face_pack": (_i, [_p, _p, _i, _i, ctypes.c_double, _p, _p]),
+    "qcd_face_unpack": (_i, [_p, _i, _p, _p]),
+    "qcd_solve_cg_many": (_i, [_i, ctypes.POINTER(_p), ctypes.POINTER(_p), ctypes.POINTER(_p),
+                               ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats), ctypes.c_longlong, _p]),
     "qcd_solve_cg_batch": (_i, [_p, ctypes.POINTER(_p), ctypes.POINTER(_p), _i, ctypes.POINTER(SolverParams),
                                 ctypes.POINTER(SolverStats), _p]),
 }
@@ -367,6 +371,41 @@ def solve_cg_batch(gauge: Gauge, xs, bs, kappas, mus=None, tols=None, maxiter: i
     return status, [{k: getattr(st[i], k) for k, _ in SolverStats._fields_} for i in range(n)]
 
 
+FACE_TO_PREV, FACE_TO_NEXT, FACE_FROM_PREV, FACE_FROM_NEXT = 0, 1, 2, 3
+
+
+def face_pack(gauge: Gauge, inp: Spinor, face: int, face_ptr: int, dagger: bool = False, sign: float = 1.0,
+              stream=None):
+    """qcd_face_pack into the device buffer at face_ptr (6 x sites-per-slice double2)."""
+    _check(lib().qcd_face_pack(gauge.handle, inp.handle, int(face), int(bool(dagger)), float(sign), _p(face_ptr),
+                               _stream(stream)), "qcd_face_pack")
+
+
+def face_unpack(out: Spinor, face: int, face_ptr: int, stream=None):
+    """qcd_face_unpack of the device buffer at face_ptr into a halo slice of `out`."""
+    _check(lib().qcd_face_unpack(out.handle, int(face), _p(face_ptr), _stream(stream)), "qcd_face_unpack")
+
+
+def solve_cg_many(gauges, xs, bs, kappas, mus=None, tols=None, maxiter: int = 20000, wait_cycles: int = 0,
+                  stream=None, raise_on_error: bool = True):
+    """FP64 even-odd CG of several systems, each on its own gauge field and
+    lattice, in one persistent launch (qcd_solve_cg_many); returns (status,
+    [stats dict])."""
+    n = len(bs)
+    if len(xs) != n or len(kappas) != n or len(gauges) != n:
+        raise ValueError("gauges, xs, bs and kappas differ in length")
+    mus = [0.0] * n if mus is None else list(mus)
+    tols = [1e-10] * n if tols is None else list(tols)
+    prm = (SolverParams * n)(*[SolverParams(float(kappas[k]), float(mus[k]), float(tols[k]), int(maxiter), 1, 0,
+                                            PREC["f64"], 18, 0.1) for k in range(n)])
+    st = (SolverStats * n)()
+    status = lib().qcd_solve_cg_many(n, _handles(gauges), _handles(xs), _handles(bs), prm, st, int(wait_cycles),
+                                     _stream(stream))
+    if raise_on_error and status != 0:
+        _check(status, "qcd_solve_cg_many")
+    return status, [{k: getattr(st[i], k) for k, _ in SolverStats._fields_} for i in range(n)]
+
+
 def solve_cg(gauge: Gauge, x: Spinor, b: Spinor, kappa: float, mu: float = 0.0, tol: float = 1e-10,
              maxiter: int = 20000, eo: bool = True, normal: bool = False, inner_prec: str = "f64",
              inner_recon: int = 12, reliable_delta: float = 0.1, stream=None, raise_on_error: bool = True):
@@ -421,10 +460,10 @@ def norm2_noalloc(x_ptr: int, n: int, result_ptr: int, stream=None):
 class Server:
     """qcd_server: concurrent even-odd solves admitted by slot and memory budget."""
 
-    def __init__(self, slots: int = 4, memory_budget: int = 32 << 30):
+    def __init__(self, slots: int = 4, memory_budget: int = 32 << 30, batch_small_sites: int = 0):
         h = _p()
-        _check(lib().qcd_server_create(ctypes.byref(ServerConfig(int(slots), int(memory_budget))), ctypes.byref(h)),
-               "qcd_server_create")
+        cfg = ServerConfig(int(slots), int(memory_budget), int(batch_small_sites))
+        _check(lib().qcd_server_create(ctypes.byref(cfg), ctypes.byref(h)), "qcd_server_create")
         self._h = h
         self._keep = {}
 

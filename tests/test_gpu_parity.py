@@ -155,6 +155,60 @@ def test_dslash_eo_low_precision(q, prec, recon, dims):
         assert err <= tol_of(prec), (prec, recon, err)
 
 
+def _round16(a, prec):
+    """float32 array rounded to FP16 or BF16 (round to nearest even), back in float32."""
+    a = np.asarray(a, dtype=np.float32)
+    if prec == "f16":
+        return a.astype(np.float16).astype(np.float32)
+    b = a.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32)
+
+
+def _stored_spinor(half, prec):
+    """The values a 16-bit half field holds: FP32, then FP16 relative to the
+    site's largest |real part| (FP16) or BF16 as is."""
+    v = np.stack([half.real, half.imag], axis=-1).astype(np.float32)  # [site, 4, 3, 2]
+    if prec == "f16":
+        m = np.abs(v).reshape(v.shape[0], -1).max(axis=1).astype(np.float32)
+        inv = np.where(m > 0, np.float32(1) / np.where(m > 0, m, 1), 0).astype(np.float32)
+        q = _round16(v * inv[:, None, None, None], prec) * m[:, None, None, None]
+    else:
+        q = _round16(v, prec)
+    q = q.astype(np.float64)
+    return q[..., 0] + 1j * q[..., 1]
+
+
+def _stored_links_recon12(U, prec):
+    """16-bit reconstruct-12 links: rows 0 and 1 rounded, row 2 rebuilt as
+    conj(row0 x row1) (in FP64 here; the GPU rebuilds in FP32)."""
+    r = np.stack([U.real, U.imag], axis=-1).astype(np.float32)
+    r = _round16(r, prec).astype(np.float64)
+    V = r[..., 0] + 1j * r[..., 1]
+    V[..., 2, :] = np.conj(np.cross(V[..., 0, :], V[..., 1, :]))
+    return V
+
+
+@pytest.mark.parametrize("prec", ["f16", "bf16"])
+def test_low_precision_bound_from_storage_rounding(q, prec):
+    """The 8u tolerance of the 16-bit tests, taken apart: a model that rounds
+    the inputs as the storage does and then computes exactly is within 2u of
+    the GPU result (the output rounding and FP32 arithmetic), and within 6u of
+    the exact result (the input and link roundings)."""
+    dims = (8, 6, 4, 10)
+    lat, U, g = gauge(q, dims, recon=12)
+    half_in = syn.to_half(syn.gaussian_spinor(dims, 13), 1)
+    si, so = q.Spinor(lat, "odd", prec), q.Spinor(lat, "even", prec)
+    si.upload(half_in)
+    q.apply_dslash(g, so, si)
+    exact = oracle.dhop_eo(U, half_in, 0)
+    model = oracle.dhop_eo(_stored_links_recon12(U, prec), _stored_spinor(half_in, prec), 0)
+    u = U_ROUND[prec]
+    assert F.rel_err(so.download(), model) <= 2 * u
+    assert F.rel_err(model, exact) <= 6 * u
+    assert F.rel_err(so.download(), exact) <= tol_of(prec)
+
+
 def test_dslash_point_source_support(q):
     """A delta source feeds exactly the 8 neighbour sites (bit-exact zeros elsewhere)."""
     dims = (6, 4, 4, 4)
