@@ -113,6 +113,9 @@ qcd_status qcd_stream_sync(void *stream);
  * call waits for the legacy default stream.  Errors: INVALID_ARG for bad
  * extents or a volume too large for 32-bit site indices; OOM. */
 qcd_status qcd_lattice_create(const int dims[4], int t_bc, qcd_lattice **out);
+/* Release the lattice.  Gauge fields and spinors created on it keep it
+ * alive: its memory is freed when the last of them is destroyed, so fields
+ * and their lattice may be destroyed in any order.  NULL is a no-op. */
 void qcd_lattice_destroy(qcd_lattice *lat);
 
 /* ------------------------------------------------------------------ gauge */
@@ -311,7 +314,11 @@ qcd_status qcd_solve_cg_batch(const qcd_gauge *g, qcd_spinor *const *x, const qc
  * lattices may run concurrently on the same gauge field); distinct x;
  * params[k].eo = 1, normal = 0, inner_prec = F64, one maxiter for all.
  * Blocks are shared out in proportion to the site counts, so each result is
- * bitwise the same alone and in any batch.  wait_cycles bounds every
+ * bitwise the same alone and in any batch.  max_blocks (0: as many as fit
+ * the GPU at once, else at least n) caps the grid, so a caller that shares
+ * the GPU with other work does not wait for all of it to be free: a
+ * cooperative launch starts only once every block is resident.  wait_cycles
+ * bounds every
  * barrier wait (0: about two seconds); when a wait runs out the call
  * returns QCD_ERR_TIMEOUT and the context stays usable.  The systems' lattice
  * handles hold the scratch fields, so calls that share a lattice must not
@@ -319,7 +326,7 @@ qcd_status qcd_solve_cg_batch(const qcd_gauge *g, qcd_spinor *const *x, const qc
  * errors as for qcd_solve_cg, per system in stats. */
 qcd_status qcd_solve_cg_many(int n, const qcd_gauge *const *gauges, qcd_spinor *const *x, const qcd_spinor *const *b,
                              const qcd_solver_params *params, qcd_solver_stats *stats, long long wait_cycles,
-                             void *stream);
+                             int max_blocks, void *stream);
 
 /* ---------------------------------------------------- time-slab split
  * The paper splits the lattice in the time direction across devices
@@ -443,6 +450,14 @@ qcd_status qcd_profile_begin(void);
 qcd_status qcd_profile_end(qcd_profile *out);
 /* Number of CUDA kernels this library has launched since it was loaded. */
 unsigned long long qcd_kernel_launches(void);
+
+/* Launch shape of the FP64 reconstruct-18 hopping kernel (one right-hand
+ * side): 0 (default) lets the autotuner choose between one thread per
+ * output site and eight (one hop each, for small lattices); 1 or 8 forces
+ * that choice for later launches (tests and benchmarks of either kernel).
+ * The paper compiles kernels per configuration (Sec. 4); here both are
+ * compiled and one is picked per lattice.  INVALID_ARG for other values. */
+qcd_status qcd_set_hop_threads(int threads_per_site);
 
 /* Host-side failure injection for tests of the error paths (no device
  * fault is involved): the next `count` calls of kind `what` fail with

@@ -445,12 +445,23 @@ cudaError_t launch_dslash(int prec, int recon, const DslashLaunch &a, cudaStream
 // first launch of a (precision, recon, batch, parity layout, extents)
 // configuration outside stream capture times the FP32/16-bit kernel with 64,
 // 128 and 256 threads per block (CUDA events, three launches each on
-// scratch fields) and keeps the fastest.  With QCD_TUNE_CACHE=<file> the
-// choices are read from and appended to that file, so later processes skip
-// the timing.
+// scratch fields) and keeps the fastest.  FP64 reconstruct-18 launches with
+// one right-hand side choose between one thread per site (64-thread blocks)
+// and the eight-lane kernel (one hop per thread, 128-thread blocks), the
+// latter winning on small lattices; a choice is stored as
+// tpb | (threads per site << 16).  With QCD_TUNE_CACHE=<file> the choices
+// are read from and appended to that file, so later processes skip the
+// timing.
 static std::mutex g_tune_mu;
 static std::map<std::string, int> g_tune;
 static bool g_tune_loaded = false;
+static std::atomic<int> g_force_tps{0};  // qcd_set_hop_threads: 0 autotuned, 1 or 8 forced
+
+static bool valid_tune(int v)
+{
+    const int tpb = v & 0xffff, tps = v >> 16;
+    return (tpb == 64 || tpb == 128 || tpb == 256) && (tps == 0 || (tps == 8 && tpb == 128));
+}
 
 static void tune_load()
 {
@@ -463,7 +474,7 @@ static void tune_load()
     char key[256];
     int v;
     while (fscanf(f, "%255s %d", key, &v) == 2)
-        if (v == 64 || v == 128 || v == 256) g_tune[key] = v;
+        if (valid_tune(v)) g_tune[key] = v;
     fclose(f);
 }
 
@@ -486,9 +497,15 @@ static std::string tune_key(const qcd_lattice *lat, int prec, int recon, int L, 
     return k;
 }
 
+constexpr int kLanes8 = 128 | (8 << 16);
+
 int tuned_tpb(const qcd_lattice *lat, const GaugeView &U, int prec, int recon, int L, bool both, cudaStream_t s)
 {
-    if (prec == QCD_PREC_F64 || prec == QCD_PREC_DF64) return 64;
+    const bool lanes8_ok = prec == QCD_PREC_F64 && recon == 18 && L == 0;
+    if ((prec == QCD_PREC_F64 && !lanes8_ok) || prec == QCD_PREC_DF64) return 64;
+    const int force = g_force_tps.load();
+    if (lanes8_ok && force == 8) return kLanes8;
+    if (lanes8_ok && force == 1) return 64;
     const std::string key = tune_key(lat, prec, recon, L, both);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -497,10 +514,11 @@ int tuned_tpb(const qcd_lattice *lat, const GaugeView &U, int prec, int recon, i
         if (it != g_tune.end()) return it->second;
     }
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return 128;
+    const int fallback = lanes8_ok ? 64 : 128;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return fallback;
     const FieldView ti = ws_field(lat, "tune_in", both ? 2 : 1, prec, L);
     const FieldView to = ws_field(lat, "tune_out", both ? 2 : 1, prec, L);
-    if (!ti.hv[0].data || !to.hv[0].data || launch_zero(ti, s) != cudaSuccess) return 128;
+    if (!ti.hv[0].data || !to.hv[0].data || launch_zero(ti, s) != cudaSuccess) return fallback;
     DslashLaunch a;
     memset(&a, 0, sizeof(a));
     a.g = lat->geom;
@@ -516,10 +534,12 @@ int tuned_tpb(const qcd_lattice *lat, const GaugeView &U, int prec, int recon, i
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    int best = 128;
+    int best = fallback;
     float best_ms = 1e30f;
-    for (int tpb : {128, 64, 256}) {
-        a.tpb = tpb;
+    const std::vector<int> cand = lanes8_ok ? std::vector<int>{64, kLanes8} : std::vector<int>{128, 64, 256};
+    for (int v : cand) {
+        a.tpb = v & 0xffff;
+        a.split = (v >> 16) == 8 ? 8 : 1;
         bool ok = launch_dslash(prec, recon, a, s) == cudaSuccess;  // warm-up
         float ms_min = 1e30f;
         for (int r = 0; r < 3 && ok; ++r) {
@@ -533,7 +553,7 @@ int tuned_tpb(const qcd_lattice *lat, const GaugeView &U, int prec, int recon, i
         note_launches(4);
         if (ok && ms_min < best_ms) {
             best_ms = ms_min;
-            best = tpb;
+            best = v;
         }
     }
     cudaEventDestroy(e0);
@@ -568,7 +588,13 @@ cudaError_t hop(const qcd_lattice *lat, const GaugeView &U, int recon, const Hop
     }
     memcpy(a.cy, h.cy.c, sizeof(a.cy));
     memcpy(a.cd, h.cd.c, sizeof(a.cd));
+    for (int k = 0; k < 4; ++k) {
+        a.cyf[k >> 1][k & 1] = (float)a.cy[k >> 1][k & 1];
+        a.cdf[k >> 1][k & 1] = (float)a.cd[k >> 1][k & 1];
+    }
+    if (h.coef && !h.coef_f) return cudaErrorInvalidValue;
     a.coef = h.coef;
+    a.coef_f = h.coef_f;
     a.coef_stride = h.coef_stride;
     if (h.plain)
         a.epi = EPI_PLAIN;
@@ -576,12 +602,15 @@ cudaError_t hop(const qcd_lattice *lat, const GaugeView &U, int recon, const Hop
         a.epi = EPI_CPLX_D;  // out = cd .* D in (real coefficients are the im = 0 case)
     else
         a.epi = h.twisted ? EPI_CPLX_YD : EPI_REAL_YD;
-    a.tpb = tuned_tpb(lat, U, h.out->prec, recon, h.out->rhs_log2, h.both, s);
+    const int cfg = tuned_tpb(lat, U, h.out->prec, recon, h.out->rhs_log2, h.both, s);
+    a.tpb = cfg & 0xffff;
+    a.split = (cfg >> 16) == 8 ? 8 : 1;
     a.reduce = h.reduce;
     a.red = h.red ? *h.red : reduction_of(lat);
     if (h.reduce) {
         const int tpb = a.tpb;
-        const size_t blocks = (size_t)(((lat->h << h.out->rhs_log2) + tpb - 1) / tpb) * (h.both ? 2 : 1);
+        const size_t blocks =
+            (size_t)((((size_t)lat->h << h.out->rhs_log2) * a.split + tpb - 1) / tpb) * (h.both ? 2 : 1);
         if (!reduction_fits(a.red, 1, h.out->rhs_log2, blocks)) return cudaErrorInvalidValue;
     }
     a.fin = h.fin;
@@ -647,6 +676,14 @@ const char *qcd_last_error(void) { return g_err; }
 const char *qcd_version(void) { return "libqcd 0.1 (sm_103a)"; }
 
 unsigned long long qcd_kernel_launches(void) { return g_launches.load(); }
+
+qcd_status qcd_set_hop_threads(int threads_per_site)
+{
+    if (threads_per_site != 0 && threads_per_site != 1 && threads_per_site != 8)
+        return fail(QCD_ERR_INVALID_ARG, "set_hop_threads: %d is not 0, 1 or 8", threads_per_site);
+    g_force_tps.store(threads_per_site);
+    return QCD_OK;
+}
 
 qcd_status qcd_debug_inject(int what, int count)
 {
@@ -733,8 +770,9 @@ qcd_status qcd_lattice_create(const int dims[4], int t_bc, qcd_lattice **out)
     g.tbc = (double)t_bc;
     lat->h = (int)h;
     lat->stride = (int)((h + 63) / 64 * 64);
-    // partials of the largest grid: 64-thread blocks over all V sites
-    lat->red_cap = 2 * (((size_t)V + 63) / 64 + 64);
+    // partials of the largest grid: 128-thread blocks over eight work items
+    // per site of all V sites (the eight-lane FP64 kernel), two values each
+    lat->red_cap = 2 * (((size_t)V + 15) / 16 + 64);
     cudaError_t e = lat_alloc(lat, (void **)&lat->red_partials, lat->red_cap * sizeof(double));
     if (e == cudaSuccess) e = lat_alloc(lat, (void **)&lat->red_counter, 64);
     if (e == cudaSuccess) e = lat_alloc(lat, (void **)&lat->red_out, 8 * sizeof(double));
@@ -758,9 +796,8 @@ qcd_status qcd_lattice_create(const int dims[4], int t_bc, qcd_lattice **out)
     return QCD_OK;
 }
 
-void qcd_lattice_destroy(qcd_lattice *lat)
+static void lattice_free(qcd_lattice *lat)
 {
-    if (!lat) return;
     if (lat->alloc_stream) {
         // stream-ordered: wait for this lattice's own stream only (its graphs
         // and staging must be idle), then free in stream order
@@ -796,6 +833,18 @@ void qcd_lattice_destroy(qcd_lattice *lat)
     delete lat;
 }
 
+static void lat_ref(const qcd_lattice *lat) { lat->refs.fetch_add(1); }
+
+static void lat_unref(const qcd_lattice *lat)
+{
+    if (lat->refs.fetch_sub(1) == 1) lattice_free(const_cast<qcd_lattice *>(lat));
+}
+
+void qcd_lattice_destroy(qcd_lattice *lat)
+{
+    if (lat) lat_unref(lat);
+}
+
 qcd_status qcd_gauge_create(const qcd_lattice *lat, qcd_prec prec, qcd_recon recon, qcd_gauge **out)
 {
     if (!lat || !out) return fail(QCD_ERR_INVALID_ARG, "gauge_create: NULL argument");
@@ -819,6 +868,7 @@ qcd_status qcd_gauge_create(const qcd_lattice *lat, qcd_prec prec, qcd_recon rec
         delete g;
         return fail(QCD_ERR_CUDA, "gauge_create: zeroing the field failed");
     }
+    lat_ref(lat);
     *out = g;
     return QCD_OK;
 }
@@ -868,11 +918,15 @@ qcd_status qcd_gauge_prepare(qcd_gauge *g, qcd_prec prec, qcd_recon recon, void 
 void qcd_gauge_destroy(qcd_gauge *g)
 {
     if (!g) return;
-    DeviceLock dl(device_mutex());
-    cudaDeviceSynchronize();
-    drop_derived(g);
-    cudaFree(g->data);
-    delete g;
+    const qcd_lattice *lat = g->lat;
+    {
+        DeviceLock dl(device_mutex());
+        cudaDeviceSynchronize();
+        drop_derived(g);
+        cudaFree(g->data);
+        delete g;
+    }
+    lat_unref(lat);
 }
 
 qcd_status qcd_spinor_bytes(const qcd_lattice *lat, qcd_parity parity, qcd_prec prec, size_t *data_bytes,
@@ -921,6 +975,7 @@ qcd_status qcd_spinor_create(const qcd_lattice *lat, qcd_parity parity, qcd_prec
         delete s;
         return fail(QCD_ERR_OOM, "spinor_create: cudaMalloc failed");
     }
+    lat_ref(lat);
     *out = s;
     return QCD_OK;
 }
@@ -953,6 +1008,7 @@ qcd_status qcd_spinor_create_ks(const qcd_lattice *lat, qcd_parity parity, qcd_p
         delete s;
         return fail(QCD_ERR_OOM, "spinor_create_ks: cudaMalloc failed");
     }
+    lat_ref(lat);
     *out = s;
     return QCD_OK;
 }
@@ -1004,6 +1060,7 @@ qcd_status qcd_spinor_wrap_device(const qcd_lattice *lat, qcd_parity parity, qcd
     s->data = data;
     s->norm = prec == QCD_PREC_F16 ? static_cast<float *>(norm) : nullptr;
     s->owns = false;
+    lat_ref(lat);
     *out = s;
     return QCD_OK;
 }
@@ -1011,10 +1068,11 @@ qcd_status qcd_spinor_wrap_device(const qcd_lattice *lat, qcd_parity parity, qcd
 void qcd_spinor_destroy(qcd_spinor *s)
 {
     if (!s) return;
-    if (s->owns && s->lat->alloc_stream) {
+    const qcd_lattice *lat = s->lat;
+    if (s->owns && lat->alloc_stream) {
         // stream-ordered lattice: freed after the work queued on its stream
-        lat_free(s->lat, s->data);
-        lat_free(s->lat, s->norm);
+        lat_free(lat, s->data);
+        lat_free(lat, s->norm);
     } else if (s->owns) {
         DeviceLock dl(device_mutex());
         cudaDeviceSynchronize();
@@ -1022,6 +1080,7 @@ void qcd_spinor_destroy(qcd_spinor *s)
         cudaFree(s->norm);
     }
     delete s;
+    lat_unref(lat);
 }
 
 qcd_status qcd_spinor_upload(qcd_spinor *s, const double *host, void *stream)

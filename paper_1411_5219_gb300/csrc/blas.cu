@@ -193,7 +193,8 @@ __global__ void __launch_bounds__(kThreads) cg_xr_kernel(const FieldView x, cons
     using R = typename SF::R;
     using RX = typename SX::R;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    double v[1] = {0.0};
+    using RedT = typename std::conditional<std::is_same<R, float>::value, float, double>::type;
+    RedT v[1] = {RedT(0)};
     if (k < nsites(x)) {
         const double alpha = stt->r[k & ((1 << x.rhs_log2) - 1)].alpha;
         const Spinor<R> pp = ld<SF>(p, k), qq = ld<SF>(q, k);
@@ -212,7 +213,7 @@ __global__ void __launch_bounds__(kThreads) cg_xr_kernel(const FieldView x, cons
             }
         st<SX>(x, k, xx);
         st<SF>(r, k, rr);
-        v[0] = (double)norm2(rr);
+        v[0] = (RedT)norm2(rr);
     }
     grid_reduce_rhs<1>(v, x.rhs_log2, red, FIN_CG_RR, stt, nullptr);
 }

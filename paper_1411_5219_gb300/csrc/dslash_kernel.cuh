@@ -21,6 +21,7 @@
 
 #include "qcd_internal.cuh"
 #include "dslash_pairs.cuh"
+#include "hop_lanes.cuh"
 
 namespace qcd {
 
@@ -285,7 +286,9 @@ __global__ void __launch_bounds__(TPB, kMinBlocks) dslash_kernel(const DslashLau
     const int e = (blockIdx.x - (a.both ? p * nbp : 0)) * blockDim.x + threadIdx.x;
     const int L = a.rhs_log2, rhs = e & ((1 << L) - 1);
     const int i = e >> L;
-    double red[1] = {0.0};
+    // fused norm: summed within the warp in float by the FP32/16-bit kernels
+    using RedT = typename std::conditional<std::is_same<R, float>::value, float, double>::type;
+    RedT red[1] = {RedT(0)};
     if (e < ne) {
         const Geom &g = a.g;
         const SpinorView &in = a.in[p];
@@ -308,7 +311,7 @@ __global__ void __launch_bounds__(TPB, kMinBlocks) dslash_kernel(const DslashLau
             const bool wf = c.t == g.L[3] - 1, wb = c.t == 0;
             nb[6] = wf ? i - (g.L[3] - 1) * g.st : i + g.st;
             nb[7] = wb ? i + (g.L[3] - 1) * g.st : i - g.st;
-            const bool anti = g.tbc < 0.0;
+            const bool anti = antiperiodic(g);
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 lb[k] = (k & 1 ? bwd : fwd) + (k >> 1);
@@ -408,12 +411,25 @@ __global__ void __launch_bounds__(TPB, kMinBlocks) dslash_kernel(const DslashLau
         // by every launch of a captured CG graph (so one graph serves all
         // kappa and mu)
         // (with a per-rhs table, the one of this element's rhs)
-        const double *cf = a.coef ? a.coef + (size_t)rhs * a.coef_stride : nullptr;
-        double cyv[2][2], cdv[2][2];
+        // The FP32 and 16-bit kernels read float copies: a double-to-float
+        // conversion would occupy the FP64 pipe once per coefficient and thread.
+        constexpr bool kF32 = std::is_same<R, float>::value;
+        using CR = typename std::conditional<kF32, float, double>::type;
+        CR cyv[2][2], cdv[2][2];
+        if constexpr (kF32) {
+            const float *cf = a.coef_f ? a.coef_f + (size_t)rhs * a.coef_stride : nullptr;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            cyv[k >> 1][k & 1] = cf ? __ldg(cf + k) : a.cy[k >> 1][k & 1];
-            cdv[k >> 1][k & 1] = cf ? __ldg(cf + 4 + k) : a.cd[k >> 1][k & 1];
+            for (int k = 0; k < 4; ++k) {
+                cyv[k >> 1][k & 1] = cf ? __ldg(cf + k) : a.cyf[k >> 1][k & 1];
+                cdv[k >> 1][k & 1] = cf ? __ldg(cf + 4 + k) : a.cdf[k >> 1][k & 1];
+            }
+        } else {
+            const double *cf = a.coef ? a.coef + (size_t)rhs * a.coef_stride : nullptr;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                cyv[k >> 1][k & 1] = cf ? __ldg(cf + k) : a.cy[k >> 1][k & 1];
+                cdv[k >> 1][k & 1] = cf ? __ldg(cf + 4 + k) : a.cd[k >> 1][k & 1];
+            }
         }
         // epilogue
         Spinor<R> out;
@@ -458,7 +474,7 @@ __global__ void __launch_bounds__(TPB, kMinBlocks) dslash_kernel(const DslashLau
             for (int s = 0; s < 4; ++s)
 #pragma unroll
                 for (int cc = 0; cc < 3; ++cc) n += out.c[s][cc].re * out.c[s][cc].re + out.c[s][cc].im * out.c[s][cc].im;
-            red[0] = (double)n;
+            red[0] = (RedT)n;
         }
     }
     if (kReduce) grid_reduce_rhs<1>(red, a.rhs_log2, a.red, a.fin, a.state, a.red_out);
@@ -467,9 +483,80 @@ __global__ void __launch_bounds__(TPB, kMinBlocks) dslash_kernel(const DslashLau
 // Dispatch over epilogue / reduction for one format pair, one dagger value
 // and one block size.  (The real-scale epilogue without y has no caller and
 // is not instantiated.)
+// FP64 reconstruct-18, one right-hand side: eight threads per site, one hop
+// each (hop_lanes.cuh), for small lattices whose time a single thread's
+// chain of FP64 hops would set.  Same epilogues and fused reduction as
+// dslash_kernel; lanes with bit 0 clear own one spin of the output.
+template <int kDagger, int kEpi, bool kReduce>
+__global__ void __launch_bounds__(128) dslash_lanes8_kernel(const DslashLaunch a)
+{
+    if (a.check_status && a.state->status != a.run_status) return;
+    const int items = a.g.h * 8;
+    const int nbp = (items + 127) / 128;
+    const int p = a.both ? (int)(blockIdx.x >= (unsigned)nbp) : a.out_parity;
+    const int w = (blockIdx.x - (a.both ? p * nbp : 0)) * 128 + threadIdx.x;
+    const bool act = w < items;
+    const int i = w >> 3, lane = w & 7;
+    cx<double> acc[12];
+    if (act) {
+        hop_lane8<false>(a.g, static_cast<const double2 *>(a.U.data), a.U.stride,
+                         static_cast<const double2 *>(a.in[p].data), a.in[p].stride, p, i, lane, kDagger != 0, acc);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[k] = mk(0.0, 0.0);
+    }
+    reduce_lanes8(acc, lane);
+    double red[1] = {0.0};
+    if (act && !(lane & 1)) {
+        const int spin = ((lane >> 2) << 1) | ((lane >> 1) & 1), chi = spin >> 1;
+        const double *cf = a.coef;
+        const cx<double> d = mk(cf ? __ldg(cf + 4 + 2 * chi) : a.cd[chi][0], cf ? __ldg(cf + 5 + 2 * chi) : a.cd[chi][1]);
+        const cx<double> cy = mk(cf ? __ldg(cf + 2 * chi) : a.cy[chi][0], cf ? __ldg(cf + 1 + 2 * chi) : a.cy[chi][1]);
+        double2 *o = static_cast<double2 *>(a.out[p].data);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int plane = 3 * spin + k;
+            cx<double> v = acc[k];
+            if (kEpi == EPI_REAL_D) {
+                v = d.re * v;
+            } else if (kEpi == EPI_CPLX_D) {
+                v = cmul(d, v);
+            } else if (kEpi == EPI_REAL_YD || kEpi == EPI_CPLX_YD) {
+                const double2 y = __ldg(static_cast<const double2 *>(a.y[p].data) + (size_t)plane * a.y[p].stride + i);
+                if (kEpi == EPI_REAL_YD)
+                    v = mk(fma(d.re, v.re, cy.re * y.x), fma(d.re, v.im, cy.re * y.y));
+                else
+                    v = cmac(cmul(cy, mk(y.x, y.y)), d, v);
+            }
+            o[(size_t)plane * a.out[p].stride + i] = make_double2(v.re, v.im);
+            if (kReduce) red[0] += v.re * v.re + v.im * v.im;
+        }
+    }
+    if (kReduce) grid_reduce_rhs<1>(red, 0, a.red, a.fin, a.state, a.red_out);
+}
+
 template <typename SF, typename GF, int D, int TPB>
 cudaError_t launch_dslash_tpb(const DslashLaunch &a, cudaStream_t s)
 {
+    if (a.split == 8) {
+        if constexpr (std::is_same<SF, SpF64>::value && GF::kRecon_ == 18) {
+            if (a.rhs_log2 != 0) return cudaErrorInvalidValue;
+            const dim3 grid(((8 * a.g.h + 127) / 128) * (a.both ? 2 : 1)), block(128);
+#define QCD_DSL8(E, RD)                                                   \
+    if (a.epi == E && a.reduce == RD) {                                   \
+        dslash_lanes8_kernel<D, E, RD><<<grid, block, 0, s>>>(a);         \
+        return cudaGetLastError();                                        \
+    }
+            QCD_DSL8(EPI_PLAIN, false)
+            QCD_DSL8(EPI_CPLX_D, false)
+            QCD_DSL8(EPI_REAL_YD, false)
+            QCD_DSL8(EPI_REAL_YD, true)
+            QCD_DSL8(EPI_CPLX_YD, false)
+            QCD_DSL8(EPI_CPLX_YD, true)
+#undef QCD_DSL8
+        }
+        return cudaErrorInvalidValue;
+    }
     const dim3 grid((((a.g.h << a.rhs_log2) + TPB - 1) / TPB) * (a.both ? 2 : 1)), block(TPB);
 #define QCD_DSL(E, RD)                                                      \
     if (a.epi == E && a.reduce == RD) {                                     \
@@ -492,7 +579,7 @@ cudaError_t launch_dslash_tpb(const DslashLaunch &a, cudaStream_t s)
 template <typename SF, typename GF, int D>
 cudaError_t launch_dslash_dag(const DslashLaunch &a, cudaStream_t s)
 {
-    if (sizeof(typename SF::R) == 8) return launch_dslash_tpb<SF, GF, D, 64>(a, s);
+    if (sizeof(typename SF::R) == 8) return launch_dslash_tpb<SF, GF, D, 64>(a, s);  // (also the 8-lane FP64 kernel)
     if constexpr (sizeof(typename SF::R) != 8) {
         if (a.tpb == 64) return launch_dslash_tpb<SF, GF, D, 64>(a, s);
         if (a.tpb == 256) return launch_dslash_tpb<SF, GF, D, 256>(a, s);

@@ -1,6 +1,7 @@
 // Handle structures behind the opaque C types (internal).
 #pragma once
 
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <shared_mutex>
@@ -9,7 +10,7 @@
 #include "qcd_ops.h"
 
 // Doubles of the pinned coefficient staging buffer: 96 per rhs, up to 32 rhs.
-constexpr int kCoefHostDoubles = 96 * 32;
+constexpr int kCoefHostDoubles = 96 * 32 * 3 / 2;
 
 struct qcd_lattice {
     int dims[4];
@@ -47,6 +48,11 @@ struct qcd_lattice {
     // destroying them never synchronises the whole device.  Every use must
     // then be ordered after `alloc_stream` (the server uses this stream only).
     cudaStream_t alloc_stream = nullptr;
+    // Held by the creator and by every gauge field and spinor on the
+    // lattice: qcd_lattice_destroy drops the creator's reference and the
+    // lattice is freed with the last one, so fields may be destroyed after
+    // their lattice in any order.
+    mutable std::atomic<int> refs{1};
 };
 
 struct qcd_gauge {
@@ -133,6 +139,7 @@ struct HopArgs {
     bool check_status;
     const Reduction *red;  // scratch of the fused reduction (nullptr: the lattice's)
     const double *coef;    // device table of cy, cd (8 doubles) read at run time, or nullptr
+    const float *coef_f;   // its float image (same layout; required with coef)
     int coef_stride;       // doubles between the tables of consecutive rhs (0: shared)
     int run_status;        // with check_status: run only under this CG status (default CG_RUNNING = 0)
 };

@@ -767,6 +767,10 @@ struct Geom {
     double tbc;     // factor of the hop that wraps in t
 };
 
+// tbc < 0 as a test of its sign bit: an integer instruction, where the
+// double comparison would take the FP64 pipe in the FP32 and 16-bit kernels.
+__device__ __forceinline__ bool antiperiodic(const Geom &g) { return __double_as_longlong(g.tbc) < 0; }
+
 // Coordinates of half-site i of parity p.
 struct SiteCoords {
     int x, y, z, t, xh;
@@ -1040,18 +1044,17 @@ __device__ __forceinline__ void grid_reduce(double (&v)[NV], const Reduction &re
 // NV values per element; the last block sums the per-block partials of each
 // (value, rhs) in block order and finalises.  All threads must call it;
 // blockDim.x must be a multiple of 32 and at most 256.
+// (grid_reduce_rhs after the sums within each warp: lane r < nrhs holds
+// the warp's sum of rhs r)
 template <int NV>
-__device__ __forceinline__ void grid_reduce_rhs(double (&v)[NV], int rhs_log2, const Reduction &red,
-                                                FinalizeKind kind, CgState *st, double *out)
+__device__ __forceinline__ void grid_reduce_rhs_warp_summed(const double (&v)[NV], int rhs_log2, const Reduction &red,
+                                                            FinalizeKind kind, CgState *st, double *out)
 {
     __shared__ double sw[NV][8][kMaxRhs];  // [value][warp][rhs]; blocks of <= 256 threads
     __shared__ double tot[NV * kMaxRhs];
     __shared__ bool is_last;
     const int n = 1 << rhs_log2;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int k = 0; k < NV; ++k)
-        for (int off = 16; off >= n; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
     if (lane < n)
 #pragma unroll
         for (int k = 0; k < NV; ++k) sw[k][warp][lane] = v[k];
@@ -1087,6 +1090,36 @@ __device__ __forceinline__ void grid_reduce_rhs(double (&v)[NV], int rhs_log2, c
     }
 }
 
+template <int NV>
+__device__ __forceinline__ void grid_reduce_rhs(double (&v)[NV], int rhs_log2, const Reduction &red,
+                                                FinalizeKind kind, CgState *st, double *out)
+{
+    const int n = 1 << rhs_log2;
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+        for (int off = 16; off >= n; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
+    grid_reduce_rhs_warp_summed<NV>(v, rhs_log2, red, kind, st, out);
+}
+
+// The same for FP32 values (the FP32 and 16-bit kernels' inner-solver
+// norms): the sums within a warp are taken in float, so a warp issues one
+// float-to-double conversion instead of five FP64 additions (FP64
+// instructions hold the FP64 pipe 64 cycles per warp); the block and grid
+// sums stay in double and in a fixed order.
+template <int NV>
+__device__ __forceinline__ void grid_reduce_rhs(float (&vf)[NV], int rhs_log2, const Reduction &red,
+                                                FinalizeKind kind, CgState *st, double *out)
+{
+    const int n = 1 << rhs_log2;
+    double v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        for (int off = 16; off >= n; off >>= 1) vf[k] += __shfl_xor_sync(0xffffffffu, vf[k], off);
+        v[k] = (double)vf[k];
+    }
+    grid_reduce_rhs_warp_summed<NV>(v, rhs_log2, red, kind, st, out);
+}
+
 // ------------------------------------------------------------------ launch API
 
 // Epilogue of the hopping kernel: out = cy .* y + cd .* (D psi), with one
@@ -1110,12 +1143,15 @@ struct DslashLaunch {
     int both;
     int rhs_log2;       // batched fields: element = site * 2^rhs_log2 + rhs
     int tpb;            // threads per block (FP32/16-bit kernels; 0: default)
+    int split;          // threads per output site: 1 (0), or 8 (FP64 reconstruct-18, one rhs)
     int dagger;
     GaugeView U;
     SpinorView in[2], out[2], y[2];
     double cy[2][2], cd[2][2];  // [chirality][re, im]
+    float cyf[2][2], cdf[2][2]; // the same rounded to float (FP32 and 16-bit kernels)
     const double *coef;         // if set: cy, cd read from this device table (8 doubles) instead
-    int coef_stride;            // doubles between the tables of consecutive rhs (0: one table for all)
+    const float *coef_f;        // its float image (same layout), read by the FP32 and 16-bit kernels
+    int coef_stride;            // entries between the tables of consecutive rhs (0: one table for all)
     EpiMode epi;
     // optional fused |out|^2 reduction
     bool reduce;

@@ -237,7 +237,10 @@ void run_batch(qcd_server *sv, int s, std::vector<Job *> &jobs)
         prm[k] = qcd_solver_params{r.kappa, r.mu, r.tol, r.maxiter, 1, 0, (qcd_prec)QCD_PREC_F64, (qcd_recon)18, r.reliable_delta};
     }
     std::vector<qcd_solver_stats> stats(n);
-    if (st == QCD_OK) st = qcd_solve_cg_many(n, g.data(), xs.data(), bs.data(), prm.data(), stats.data(), 0, stream);
+    // the full resident grid (capped at 32 blocks, to start sooner beside
+    // the other slots' kernels, it served 8^3x4 requests at half the rate)
+    if (st == QCD_OK)
+        st = qcd_solve_cg_many(n, g.data(), xs.data(), bs.data(), prm.data(), stats.data(), 0, 0, stream);
     const bool ran = st == QCD_OK || st == QCD_ERR_NOT_CONVERGED || st == QCD_ERR_BREAKDOWN;
     qcd_status st2 = QCD_OK;
     if (ran)

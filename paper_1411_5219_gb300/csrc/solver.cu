@@ -37,6 +37,7 @@ struct OpCtx {
     bool eo;
     const Reduction *red;  // scratch of the fused |Mhat p|^2 reduction
     const double *coef;    // device table of the epilogue coefficients, kCoefPerRhs doubles per rhs
+    const float *coef_f;   // the same table rounded to float (read by the FP32 and 16-bit kernels)
 };
 
 // Per right-hand side, the solve reads every kappa- and mu-dependent
@@ -89,6 +90,7 @@ HopArgs table_hop(const OpCtx &c, int off)
 {
     HopArgs h{};
     h.coef = c.coef + off;
+    h.coef_f = c.coef_f + off;
     h.coef_stride = kCoefPerRhs;
     h.twisted = c.tw;
     return h;
@@ -554,19 +556,26 @@ qcd_status qcd::solve_impl(const qcd_gauge *g, qcd_spinor *const *x, const qcd_s
     // every kappa/mu-dependent coefficient lives in a device table (one block
     // per rhs; padding rhs repeat system 0), so the cached CG graph depends
     // on neither
-    double *coef = static_cast<double *>(workspace(lat, "cg_coef", (size_t)kMaxRhs * kCoefPerRhs * sizeof(double)));
+    // (the doubles of kMaxRhs blocks, then their float image)
+    constexpr size_t kTab = (size_t)kMaxRhs * kCoefPerRhs;
+    double *coef = static_cast<double *>(workspace(lat, "cg_coef", kTab * (sizeof(double) + sizeof(float))));
     if (!coef) return fail(QCD_ERR_OOM, "solve_cg: workspace");
     c.coef = coef;
+    c.coef_f = reinterpret_cast<const float *>(coef + kTab);
     {
         // staged in the lattice's pinned buffer: the previous solve on this
         // lattice synchronised its stream before returning, so the buffer is free
-        static_assert(kCoefPerRhs * kMaxRhs <= kCoefHostDoubles, "coefficient staging buffer too small");
+        static_assert(kTab * 3 / 2 <= (size_t)kCoefHostDoubles, "coefficient staging buffer too small");
         double *table = lat->coef_host;
+        float *table_f = reinterpret_cast<float *>(table + kTab);
         for (int k = 0; k < N; ++k) {
             const qcd_solver_params &q = prm[k < nrhs ? k : 0];
             coef_block(table + (size_t)k * kCoefPerRhs, c.eo, q.kappa, 2.0 * q.kappa * q.mu);
         }
+        for (size_t j = 0; j < (size_t)N * kCoefPerRhs; ++j) table_f[j] = (float)table[j];
         QCD_TRY(cudaMemcpyAsync(coef, table, (size_t)N * kCoefPerRhs * sizeof(double), cudaMemcpyHostToDevice, s),
+                "solve_cg: coefficients");
+        QCD_TRY(cudaMemcpyAsync(coef + kTab, table_f, (size_t)N * kCoefPerRhs * sizeof(float), cudaMemcpyHostToDevice, s),
                 "solve_cg: coefficients");
     }
 
@@ -659,8 +668,9 @@ qcd_status qcd::solve_impl(const qcd_gauge *g, qcd_spinor *const *x, const qcd_s
 
     qcd_status result = QCD_OK;
     if (!profiling_active()) {
-        // choose the inner kernels' launch shape before it is frozen in the graph
+        // choose the kernels' launch shapes before they are frozen in the graph
         tuned_tpb(lat, Us, sp, srecon, L, !c.eo, s);
+        if (mixed) tuned_tpb(lat, Uh, QCD_PREC_F64, g->recon, L, !c.eo, s);
         cudaGraphExec_t exec = nullptr;
         if (cg_graph(lat, F, &exec) != QCD_OK) {
             // the capture failed (e.g. invalidated by another thread): run

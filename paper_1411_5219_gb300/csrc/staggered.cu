@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(128) dslash_ks_kernel(const KsLaunch a)
     const bool wf = c.t == g.L[3] - 1, wb = c.t == 0;
     nb[6] = wf ? i - (g.L[3] - 1) * g.st : i + g.st;
     nb[7] = wb ? i + (g.L[3] - 1) * g.st : i - g.st;
-    const bool anti = g.tbc < 0.0;
+    const bool anti = antiperiodic(g);
     // staggered phases of the output site
     const int eta[4] = {1, (c.x & 1) ? -1 : 1, ((c.x + c.y) & 1) ? -1 : 1, ((c.x + c.y + c.z) & 1) ? -1 : 1};
     Colour<R> acc;

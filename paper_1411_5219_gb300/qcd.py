@@ -91,6 +91,7 @@ _SIGS = {
     "qcd_profile_end": (_i, [ctypes.POINTER(Profile)]),
     "qcd_kernel_launches": (ctypes.c_ulonglong, []),
     "qcd_debug_inject": (_i, [_i, _i]),
+    "qcd_set_hop_threads": (_i, [_i]),
     "qcd_norm2_noalloc": (_i, [_p, ctypes.c_size_t, _p, _p]),
     "qcd_server_create": (_i, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_p)]),
     "qcd_server_add_gauge": (_i, [_p, _p, ctypes.POINTER(_i)]),
@@ -104,7 +105,8 @@ _SIGS = {
     "qcd_face_pack": (_i, [_p, _p, _i, _i, ctypes.c_double, _p, _p]),
     "qcd_face_unpack": (_i, [_p, _i, _p, _p]),
     "qcd_solve_cg_many": (_i, [_i, ctypes.POINTER(_p), ctypes.POINTER(_p), ctypes.POINTER(_p),
-                               ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats), ctypes.c_longlong, _p]),
+                               ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats), ctypes.c_longlong, _i,
+                               _p]),
     "qcd_solve_cg_batch": (_i, [_p, ctypes.POINTER(_p), ctypes.POINTER(_p), _i, ctypes.POINTER(SolverParams),
                                 ctypes.POINTER(SolverStats), _p]),
 }
@@ -387,6 +389,7 @@ def face_unpack(out: Spinor, face: int, face_ptr: int, stream=None):
 
 
 def solve_cg_many(gauges, xs, bs, kappas, mus=None, tols=None, maxiter: int = 20000, wait_cycles: int = 0,
+                  max_blocks: int = 0,
                   stream=None, raise_on_error: bool = True):
     """FP64 even-odd CG of several systems, each on its own gauge field and
     lattice, in one persistent launch (qcd_solve_cg_many); returns (status,
@@ -400,7 +403,7 @@ def solve_cg_many(gauges, xs, bs, kappas, mus=None, tols=None, maxiter: int = 20
                                             PREC["f64"], 18, 0.1) for k in range(n)])
     st = (SolverStats * n)()
     status = lib().qcd_solve_cg_many(n, _handles(gauges), _handles(xs), _handles(bs), prm, st, int(wait_cycles),
-                                     _stream(stream))
+                                     int(max_blocks), _stream(stream))
     if raise_on_error and status != 0:
         _check(status, "qcd_solve_cg_many")
     return status, [{k: getattr(st[i], k) for k, _ in SolverStats._fields_} for i in range(n)]
@@ -443,6 +446,12 @@ NORM2_NOALLOC_MAX = 16_777_216
 
 
 INJECT_SPINOR_CREATE = 1
+
+
+def set_hop_threads(threads_per_site: int):
+    """qcd_set_hop_threads: 0 autotuned, 1 or 8 threads per site forced for the
+    FP64 reconstruct-18 hopping kernel."""
+    _check(lib().qcd_set_hop_threads(int(threads_per_site)), "qcd_set_hop_threads")
 
 
 def debug_inject(what: int, count: int):

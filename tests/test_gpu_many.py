@@ -138,3 +138,19 @@ def test_server_batches_small_requests(q):
     assert max(starts.count(t) for t in starts) >= 2  # at least one batch of two or more
     for (b, kap), x in zip(reqs, xs):
         assert schur_residual_oracle(U, b, x, kap, 0.0) <= 1.5e-10
+
+
+def test_many_grid_cap_keeps_the_bits(q, problems):
+    """A grid capped at one block per system (max_blocks = n) gives the same
+    bits as the full resident grid: reductions are summed per fixed chunk."""
+    probs = problems[:3]
+    _, _, full = _solve(q, probs)
+    xs = [q.Spinor(p["lat"], "full", "f64") for p in probs]
+    status, _ = q.solve_cg_many([p["g"] for p in probs], xs, [p["bs"] for p in probs],
+                                [p["kappa"] for p in probs], [p["mu"] for p in probs], [p["tol"] for p in probs],
+                                max_blocks=len(probs))
+    assert status == 0
+    for a, x in zip(full, xs):
+        assert np.array_equal(a, x.download())
+    with pytest.raises(q.QcdError):
+        q.solve_cg_many([p["g"] for p in probs], xs, [p["bs"] for p in probs], [0.13] * 3, max_blocks=2)

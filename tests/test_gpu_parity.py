@@ -260,6 +260,33 @@ def test_apply_schur_low_precision(q, prec):
     assert F.rel_err(eo_.download(), oracle.apply_mhat(U, xe, kappa, mu)) <= tol_of(prec)
 
 
+def test_lattice_destroyed_before_its_fields(q):
+    """Fields keep their lattice alive: destroying the lattice first leaves
+    its spinors and gauge field usable, and destroying them afterwards (in
+    any order, as a cyclic garbage collection may) frees it."""
+    dims = (4, 4, 4, 4)
+    lat = q.Lattice(dims, -1)
+    U = syn.gauge_field(dims, 0.3, 1301)
+    g = q.Gauge(lat, "f64", 18)
+    g.upload(U)
+    psi = syn.gaussian_spinor(dims, 1302)
+    si, so = q.Spinor(lat, "odd", "f64"), q.Spinor(lat, "even", "f64")
+    si.upload(syn.to_half(psi, 1))
+    lat.close()
+    q.apply_dslash(g, so, si)
+    assert F.rel_err(so.download(), oracle.dhop_eo(U, syn.to_half(psi, 1), 0)) <= 1e-13
+    si.close()
+    g.close()
+    so.close()
+    # a spinor outliving its lattice still uploads and downloads
+    lat2 = q.Lattice(dims, -1)
+    s2 = q.Spinor(lat2, "full", "f64")
+    lat2.close()
+    s2.upload(psi)
+    assert np.array_equal(s2.download(), psi)
+    s2.close()
+
+
 def test_invalid_arguments_rejected(q):
     lat, U, g = gauge(q, (4, 4, 4, 4))
     a, b = q.Spinor(lat, "even", "f64"), q.Spinor(lat, "even", "f64")
