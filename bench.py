@@ -185,7 +185,7 @@ class Problem:
 
     def solve(self, qcd, inner="f64", recon=12, eo=True, normal=False):
         return qcd.solve_cg(self.gauge, self.x, self.b, self.kappa, self.mu, tol=TOL, eo=eo, normal=normal,
-                            inner_prec=inner, inner_recon=recon, reliable_delta=0.1)
+                            inner_prec=inner, inner_recon=recon)
 
 
 class L2Flush:

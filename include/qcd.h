@@ -252,7 +252,8 @@ typedef struct {
     qcd_prec inner_prec;   /* F64: plain FP64 CG; F32/F16/BF16/DF64: inner iterations in that precision with FP64
                               reliable updates (DF64 accumulates its correction in DF64, the others in FP32) */
     qcd_recon inner_recon; /* link storage of the inner (sloppy) operator (DF64 always uses 18) */
-    double reliable_delta; /* mixed: reliable update when |r| < delta * max|r| since the last one (e.g. 0.1) */
+    double reliable_delta; /* mixed: reliable update when |r| < delta * max|r| since the last one, in (0, 1);
+                              0 chooses by inner precision: F32 1e-3, F16 1e-2, BF16 0.1, DF64 1e-4 */
 } qcd_solver_params;
 
 typedef struct {
@@ -388,7 +389,7 @@ typedef struct {
     int maxiter;
     qcd_prec inner_prec;   /* as qcd_solver_params (even-odd solve of M x = b) */
     qcd_recon inner_recon;
-    double reliable_delta;
+    double reliable_delta;  /* as qcd_solver_params (0: by inner precision) */
     const double *b_host;  /* full source, host layout; valid until the request completes */
     double *x_host;        /* full solution, written before completion */
 } qcd_request;

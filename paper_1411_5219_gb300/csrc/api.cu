@@ -1,5 +1,6 @@
 // C ABI of libqcd: handles, host<->device transfer, operator application.
 // Declarations and argument conventions are in include/qcd.h.
+#include <algorithm>
 #include <atomic>
 #include <cstdlib>
 #include <cstdarg>
@@ -772,9 +773,13 @@ qcd_status qcd_lattice_create(const int dims[4], int t_bc, qcd_lattice **out)
     lat->stride = (int)((h + 63) / 64 * 64);
     // partials of the largest grid: 128-thread blocks over eight work items
     // per site of all V sites (the eight-lane FP64 kernel), two values each
-    lat->red_cap = 2 * (((size_t)V + 15) / 16 + 64);
+    const size_t bmax = ((size_t)V + 15) / 16;
+    lat->red_cap = std::max(red_partials_needed(2, bmax), red_partials_needed(1, bmax));
+    // tickets: one per group of the largest grid that shares them (64-thread
+    // blocks over a batch of kMaxRhs full fields), and the final one
+    const size_t counter_bytes = ((4 * (1 + (size_t)red_group_size((unsigned)(V * kMaxRhs / 64 + 1), 1)) + 255) / 256) * 256;
     cudaError_t e = lat_alloc(lat, (void **)&lat->red_partials, lat->red_cap * sizeof(double));
-    if (e == cudaSuccess) e = lat_alloc(lat, (void **)&lat->red_counter, 64);
+    if (e == cudaSuccess) e = lat_alloc(lat, (void **)&lat->red_counter, counter_bytes);
     if (e == cudaSuccess) e = lat_alloc(lat, (void **)&lat->red_out, 8 * sizeof(double));
     if (e == cudaSuccess) e = lat_alloc(lat, (void **)&lat->red_out_big, 2 * kMaxRhs * sizeof(double));
     if (e == cudaSuccess) e = lat_alloc(lat, (void **)&lat->state, sizeof(CgState));
@@ -784,7 +789,7 @@ qcd_status qcd_lattice_create(const int dims[4], int t_bc, qcd_lattice **out)
         if (e == cudaSuccess) e = cudaMallocHost(&lat->state_host, sizeof(CgState));
         if (e == cudaSuccess) e = cudaMallocHost(&lat->coef_host, kCoefHostDoubles * sizeof(double));
     }
-    if (e == cudaSuccess) e = lat_zero(lat, lat->red_counter, 64);
+    if (e == cudaSuccess) e = lat_zero(lat, lat->red_counter, counter_bytes);
     if (e == cudaSuccess) e = lat_zero(lat, lat->state, sizeof(CgState));
     if (e != cudaSuccess) {
         qcd_status st = check_cuda(e, "lattice_create");
@@ -1203,7 +1208,9 @@ qcd_status qcd_apply_dslash_multi(const qcd_gauge *g, qcd_spinor *const *out, co
     const FieldView bi = ws_field(lat, "dm_in", nh, prec, L), bo = ws_field(lat, "dm_out", nh, prec, L);
     if (!bi.hv[0].data || !bo.hv[0].data) return fail(QCD_ERR_OOM, "apply_dslash_multi: workspace");
     cudaError_t e = launch_zero(bi, s);
-    for (int k = 0; k < nrhs && e == cudaSuccess; ++k) e = launch_batch_copy(bi, view_of(in[k]), k, 1, s);
+    FieldView pv[kMaxRhs];
+    for (int k = 0; k < nrhs; ++k) pv[k] = view_of(in[k]);
+    if (e == cudaSuccess) e = launch_batch_copy(bi, pv, nrhs, 1, s);
     if (e != cudaSuccess) return check_cuda(e, "apply_dslash_multi: gather");
     HopArgs h{};
     h.out = &bo;
@@ -1214,7 +1221,8 @@ qcd_status qcd_apply_dslash_multi(const qcd_gauge *g, qcd_spinor *const *out, co
     h.plain = true;
     h.fin = FIN_STORE;
     e = hop(lat, U, g->recon, h, s);
-    for (int k = 0; k < nrhs && e == cudaSuccess; ++k) e = launch_batch_copy(bo, view_of(out[k]), k, 0, s);
+    for (int k = 0; k < nrhs; ++k) pv[k] = view_of(out[k]);
+    if (e == cudaSuccess) e = launch_batch_copy(bo, pv, nrhs, 0, s);
     return check_cuda(e, "apply_dslash_multi");
 }
 

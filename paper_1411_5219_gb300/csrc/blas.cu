@@ -305,19 +305,22 @@ __global__ void __launch_bounds__(kThreads) cg_verify_kernel(const FieldView f, 
     grid_reduce_rhs<1>(v, f.rhs_log2, red, FIN_CG_TRUE, stt, nullptr);
 }
 
-// batched[(i << L) | rhs] <-> plain[i] over both halves
+// batched[(i << L) | rhs] <-> plain[rhs][i] for rhs < n, over both halves,
+// one thread per batched element: a warp reads (or writes) consecutive
+// batched elements, and the same few sites of each plain field.
 template <typename SF>
-__global__ void __launch_bounds__(kThreads) batch_copy_kernel(const FieldView b, const FieldView pl, const int rhs,
+__global__ void __launch_bounds__(kThreads) batch_copy_kernel(const FieldView b, const PlainSet pl, const int n,
                                                               const int to_batch)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nsites(pl)) return;
-    const int hh = k >= pl.h, i = k - hh * pl.h;
-    const int e = (i << b.rhs_log2) | rhs;
+    if (k >= nsites(b)) return;
+    const int hh = k >= b.h, e = k - hh * b.h;
+    const int rhs = e & ((1 << b.rhs_log2) - 1), i = e >> b.rhs_log2;
+    if (rhs >= n) return;
     if (to_batch)
-        SF::store(b.hv[hh], e, SF::load(pl.hv[hh], i));
+        SF::store(b.hv[hh], e, SF::load(pl.f[rhs].hv[hh], i));
     else
-        SF::store(pl.hv[hh], i, SF::load(b.hv[hh], e));
+        SF::store(pl.f[rhs].hv[hh], i, SF::load(b.hv[hh], e));
 }
 
 }  // namespace
@@ -359,11 +362,17 @@ cudaError_t launch_convert(const FieldView &dst, const FieldView &src, cudaStrea
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_copy(const FieldView &batched, const FieldView &plain, int rhs, int to_batch, cudaStream_t s)
+cudaError_t launch_batch_copy(const FieldView &batched, const FieldView *plain, int n, int to_batch, cudaStream_t s)
 {
-    if (batched.prec != plain.prec || batched.nh != plain.nh) return cudaErrorInvalidValue;
-    QCD_SP_CASES(plain.prec, SF,
-                 batch_copy_kernel<SF><<<grid_of(plain), kThreads, 0, s>>>(batched, plain, rhs, to_batch));
+    if (n < 1 || n > kMaxRhs || n > (1 << batched.rhs_log2)) return cudaErrorInvalidValue;
+    PlainSet pl;
+    for (int k = 0; k < n; ++k) {
+        if (batched.prec != plain[k].prec || batched.nh != plain[k].nh || plain[k].h << batched.rhs_log2 != batched.h)
+            return cudaErrorInvalidValue;
+        pl.f[k] = plain[k];
+    }
+    QCD_SP_CASES(batched.prec, SF,
+                 batch_copy_kernel<SF><<<grid_of(batched), kThreads, 0, s>>>(batched, pl, n, to_batch));
     note_launches();
     return cudaGetLastError();
 }

@@ -341,8 +341,8 @@ __global__ void __launch_bounds__(TPB, kMinBlocks) dslash_kernel(const DslashLau
             ru = ru_n;                                                     \
         }                                                                  \
     }
-        if constexpr (is_sp16<SF>::value) {
-            // 16-bit spinors: packed FP32 arithmetic on the two spins
+        if constexpr (uses_pairs<SF>::value) {
+            // 16-bit and FP32 spinors: packed FP32 arithmetic on the two spins
             AccPairs ap;
 #define QCD_HOP16(K, MU, S, ADJ, FIRST)                                      \
     {                                                                      \
@@ -410,25 +410,44 @@ __global__ void __launch_bounds__(TPB, kMinBlocks) dslash_kernel(const DslashLau
         // epilogue coefficients: kernel parameters, or a device table shared
         // by every launch of a captured CG graph (so one graph serves all
         // kappa and mu)
-        // (with a per-rhs table, the one of this element's rhs)
-        // The FP32 and 16-bit kernels read float copies: a double-to-float
-        // conversion would occupy the FP64 pipe once per coefficient and thread.
+        // (with a per-rhs table, the one of this element's rhs).  The FP32 and
+        // 16-bit kernels read float copies: a double-to-float conversion would
+        // occupy the FP64 pipe once per coefficient and thread.  The source is
+        // chosen by a branch on the kernel parameter: a per-thread select
+        // between a table load and a parameter cost the FP32 epilogue
+        // variants ~70 registers (226 instead of 155).
         constexpr bool kF32 = std::is_same<R, float>::value;
         using CR = typename std::conditional<kF32, float, double>::type;
         CR cyv[2][2], cdv[2][2];
         if constexpr (kF32) {
-            const float *cf = a.coef_f ? a.coef_f + (size_t)rhs * a.coef_stride : nullptr;
+            if (a.coef_f) {
+                const float *cf = a.coef_f + (size_t)rhs * a.coef_stride;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                cyv[k >> 1][k & 1] = cf ? __ldg(cf + k) : a.cyf[k >> 1][k & 1];
-                cdv[k >> 1][k & 1] = cf ? __ldg(cf + 4 + k) : a.cdf[k >> 1][k & 1];
+                for (int k = 0; k < 4; ++k) {
+                    cyv[k >> 1][k & 1] = __ldg(cf + k);
+                    cdv[k >> 1][k & 1] = __ldg(cf + 4 + k);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    cyv[k >> 1][k & 1] = a.cyf[k >> 1][k & 1];
+                    cdv[k >> 1][k & 1] = a.cdf[k >> 1][k & 1];
+                }
             }
         } else {
-            const double *cf = a.coef ? a.coef + (size_t)rhs * a.coef_stride : nullptr;
+            if (a.coef) {
+                const double *cf = a.coef + (size_t)rhs * a.coef_stride;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                cyv[k >> 1][k & 1] = cf ? __ldg(cf + k) : a.cy[k >> 1][k & 1];
-                cdv[k >> 1][k & 1] = cf ? __ldg(cf + 4 + k) : a.cd[k >> 1][k & 1];
+                for (int k = 0; k < 4; ++k) {
+                    cyv[k >> 1][k & 1] = __ldg(cf + k);
+                    cdv[k >> 1][k & 1] = __ldg(cf + 4 + k);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    cyv[k >> 1][k & 1] = a.cy[k >> 1][k & 1];
+                    cdv[k >> 1][k & 1] = a.cd[k >> 1][k & 1];
+                }
             }
         }
         // epilogue

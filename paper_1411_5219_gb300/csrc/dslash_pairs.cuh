@@ -1,4 +1,4 @@
-// The hop of the 16-bit hopping kernels in packed FP32 arithmetic.
+// The hop of the 16-bit and FP32 hopping kernels in packed FP32 arithmetic.
 //
 // The two spin components of a half spinor are multiplied by the same link,
 // so they form the two lanes of an FP32 pair: every multiply-add of the
@@ -21,6 +21,12 @@ template <typename SF>
 struct is_sp16 : std::false_type {};
 template <typename H, bool N>
 struct is_sp16<Sp16<H, N>> : std::true_type {};
+
+// Formats whose hop runs in packed FP32 pairs (16-bit and FP32 spinors).
+template <typename SF>
+struct uses_pairs : is_sp16<SF> {};
+template <>
+struct uses_pairs<SpF32> : std::true_type {};
 
 __device__ __forceinline__ float2 bc(float x) { return make_float2(x, x); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
@@ -58,22 +64,37 @@ __device__ __forceinline__ uint32_t word16(const uint4 (&w)[3], int k)
     return (k & 3) == 0 ? p.x : (k & 3) == 1 ? p.y : (k & 3) == 2 ? p.z : p.w;
 }
 
-// Spin projection of a 16-bit spinor (unscaled) straight from its words:
-// lane 0 is h_0 = psi_0 + ..., lane 1 is h_1 = psi_1 + ...; the lower spins
-// enter in the order (3, 2) for x and y, (2, 3) for z and t.
-template <typename H, int MU, int S>
-__device__ __forceinline__ HalfPairs project_pairs(const uint4 (&w)[3])
+// FP32 parts of spinor component k = 3 spin + colour of a fetched site.
+template <typename SF>
+struct PairSrc;
+template <typename H, bool N>
+struct PairSrc<Sp16<H, N>> {
+    using Raw = typename Sp16<H, N>::Raw;
+    __device__ __forceinline__ static float re(const Raw &r, int k) { return Half16Parts<H>::re(word16<H>(r.w, k)); }
+    __device__ __forceinline__ static float im(const Raw &r, int k) { return Half16Parts<H>::im(word16<H>(r.w, k)); }
+};
+template <>
+struct PairSrc<SpF32> {
+    using Raw = SpF32::Raw;  // component k in float4 k / 2, (x, y) or (z, w)
+    __device__ __forceinline__ static float re(const Raw &r, int k) { return k & 1 ? r.d[k >> 1].z : r.d[k >> 1].x; }
+    __device__ __forceinline__ static float im(const Raw &r, int k) { return k & 1 ? r.d[k >> 1].w : r.d[k >> 1].y; }
+};
+
+// Spin projection of a fetched spinor (16-bit ones unscaled) straight from
+// its storage: lane 0 is h_0 = psi_0 + ..., lane 1 is h_1 = psi_1 + ...; the
+// lower spins enter in the order (3, 2) for x and y, (2, 3) for z and t.
+template <typename SF, int MU, int S>
+__device__ __forceinline__ HalfPairs project_pairs(const typename SF::Raw &w)
 {
-    using P = Half16Parts<H>;
+    using P = PairSrc<SF>;
     constexpr int b0 = MU <= 1 ? 3 : 2, b1 = MU <= 1 ? 2 : 3;
     constexpr float s = (float)S;
     HalfPairs h;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const uint32_t a0 = word16<H>(w, c), a1 = word16<H>(w, 3 + c);
-        const uint32_t x0 = word16<H>(w, 3 * b0 + c), x1 = word16<H>(w, 3 * b1 + c);
-        const float2 ar = make_float2(P::re(a0), P::re(a1)), ai = make_float2(P::im(a0), P::im(a1));
-        const float2 xr = make_float2(P::re(x0), P::re(x1)), xi = make_float2(P::im(x0), P::im(x1));
+        const int a0 = c, a1 = 3 + c, x0 = 3 * b0 + c, x1 = 3 * b1 + c;
+        const float2 ar = make_float2(P::re(w, a0), P::re(w, a1)), ai = make_float2(P::im(w, a0), P::im(w, a1));
+        const float2 xr = make_float2(P::re(w, x0), P::re(w, x1)), xi = make_float2(P::im(w, x0), P::im(w, x1));
         if (MU == 0) {  // h = (psi0 + S i psi3, psi1 + S i psi2)
             h.r[c] = fma2(xi, make_float2(-s, -s), ar);
             h.i[c] = fma2(xr, make_float2(s, s), ai);
@@ -184,8 +205,7 @@ template <typename SF, typename GF, int MU, int S, bool kAdj, bool kFirst>
 __device__ __forceinline__ void hop_pairs(AccPairs &acc, const typename SF::Raw &rs, const typename GF::Raw &ru,
                                           bool flip)
 {
-    using H = typename SF::H16;
-    const HalfPairs h = project_pairs<H, MU, S>(rs.w);
+    const HalfPairs h = project_pairs<SF, MU, S>(rs);
     const HalfPairs v = su3_pairs<kAdj>(GF::decode(ru), h);
     const float sc = SF::scale(rs);
     accumulate_pairs<MU, S, kFirst>(acc, v, flip ? -sc : sc);

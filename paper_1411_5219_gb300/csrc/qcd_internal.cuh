@@ -817,20 +817,45 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double *smem /* NV * 
     }
 }
 
-// Scratch of a grid-wide reduction: one partial per block and a ticket
-// counter; the last block to finish sums the partials in block order, so
-// the result does not depend on scheduling.
+// Scratch of a grid-wide reduction in up to two levels: one partial per
+// block; blocks form groups of red_group_size(gridDim.x, P) consecutive
+// blocks (P reduced quantities), and the last block of a group to finish
+// sums the group's partials in block order; with several groups, the last
+// group to finish then sums the group sums in group order.  The result does
+// not depend on scheduling, and no block sums more than about 2048 values
+// (or sqrt(gridDim.x) per quantity): a single last block summing every
+// partial took longer than the kernel itself for batched fields.
 struct Reduction {
-    double *partials;   // >= NV * nrhs * gridDim.x doubles
-    unsigned *counter;  // zero before the launch; reset to zero by the last block
+    double *partials;   // >= red_partials_needed(NV * nrhs, gridDim.x) doubles
+    unsigned *counter;  // 1 + groups tickets, zero before the launch; reset by the finishing blocks
     size_t cap;         // capacity of partials in doubles (checked on the host before each launch)
 };
+
+// Blocks per group for P reduced quantities: a power of two >= 64 and
+// >= 2048 / P (so one level suffices for small grids), with at most as many
+// groups as blocks per group.  Not smaller for more blocks or fewer
+// quantities.
+__host__ __device__ inline unsigned red_group_size(unsigned blocks, unsigned P)
+{
+    unsigned g = 64;
+    while (g * P < 2048) g <<= 1;
+    while ((blocks + g - 1) / g > g) g <<= 1;
+    return g;
+}
+// Doubles of partials for `quantities` reduced values (values x rhs) over
+// at most `blocks` blocks: the block partials, then the group sums (fewer
+// than the group size, which does not decrease with the block count, so
+// the bound holds for every smaller grid too).
+inline size_t red_partials_needed(size_t quantities, size_t blocks)
+{
+    return quantities * (blocks + red_group_size((unsigned)blocks, (unsigned)quantities));
+}
 
 // Host check: a reducing launch of `blocks` blocks with NV values for 2^L
 // right-hand sides fits the partials buffer.
 inline bool reduction_fits(const Reduction &r, int nv, int rhs_log2, size_t blocks)
 {
-    return (size_t)nv * ((size_t)1 << rhs_log2) * blocks <= r.cap;
+    return blocks < (1u << 31) && red_partials_needed((size_t)nv << rhs_log2, blocks) <= r.cap;
 }
 
 // Device-resident CG state for nrhs right-hand sides solved together.
@@ -1005,45 +1030,48 @@ __device__ __forceinline__ void cg_finalize_rhs(FinalizeKind kind, const double 
     }
 }
 
-// Grid-wide deterministic reduction of NV doubles per thread with the
-// last-block pattern (one value set for the whole grid).  All threads of
-// the block must call it.
-template <int NV>
-__device__ __forceinline__ void grid_reduce(double (&v)[NV], const Reduction &red, double *out)
-{
-    __shared__ double smem[NV * 32];
-    __shared__ bool is_last;
-    block_sum<NV>(v, smem);
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) red.partials[(size_t)k * gridDim.x + blockIdx.x] = v[k];
-        __threadfence();
-        const unsigned ticket = atomicAdd(red.counter, 1u);
-        is_last = (ticket == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-    double s[NV];
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        s[k] = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s[k] += __ldcg(red.partials + (size_t)k * gridDim.x + b);
-    }
-    block_sum<NV>(s, smem);
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) out[k] = s[k];
-        *red.counter = 0u;
-    }
-}
-
 // Grid-wide reduction segmented by right-hand side: element e of a batched
 // field belongs to rhs e & (nrhs - 1) (nrhs a power of two <= 32, the rhs
 // index fastest), so in a warp the lanes of one rhs are lane & (nrhs - 1).
 // NV values per element; the last block sums the per-block partials of each
 // (value, rhs) in block order and finalises.  All threads must call it;
 // blockDim.x must be a multiple of 32 and at most 256.
+// Sums of P rows of `count` doubles (row q at src + q * stride), by every
+// thread of the block: T = blockDim / P threads per row (at least one; P and
+// blockDim powers of two), each taking every T-th element from its offset
+// with four accumulators (loads in flight), then the T sums of a row added
+// by a fixed binary tree into res[q] (shared).  The order is fixed, so the
+// sums are reproducible.
+__device__ __forceinline__ void block_row_sums(const double *src, size_t stride, int P, unsigned count,
+                                               double *res, double *scratch /* blockDim.x */)
+{
+    const int T = (int)blockDim.x >= P ? (int)blockDim.x / P : 1;
+    const int rows_per_pass = (int)blockDim.x / T;
+    for (int q0 = 0; q0 < P; q0 += rows_per_pass) {
+        const int q = q0 + (int)threadIdx.x / T, j = (int)threadIdx.x % T;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        if (q < P) {
+            const double *row = src + (size_t)q * stride;
+            unsigned b = j;
+            for (; b + 3u * T < count; b += 4u * T) {
+                a0 += __ldcg(row + b);
+                a1 += __ldcg(row + b + T);
+                a2 += __ldcg(row + b + 2u * T);
+                a3 += __ldcg(row + b + 3u * T);
+            }
+            for (; b < count; b += T) a0 += __ldcg(row + b);
+        }
+        scratch[threadIdx.x] = (a0 + a1) + (a2 + a3);
+        __syncthreads();
+        for (int off = T >> 1; off > 0; off >>= 1) {
+            if (j < off) scratch[threadIdx.x] += scratch[threadIdx.x + off];
+            __syncthreads();
+        }
+        if (j == 0 && q < P) res[q] = scratch[threadIdx.x];
+        __syncthreads();
+    }
+}
+
 // (grid_reduce_rhs after the sums within each warp: lane r < nrhs holds
 // the warp's sum of rhs r)
 template <int NV>
@@ -1052,35 +1080,49 @@ __device__ __forceinline__ void grid_reduce_rhs_warp_summed(const double (&v)[NV
 {
     __shared__ double sw[NV][8][kMaxRhs];  // [value][warp][rhs]; blocks of <= 256 threads
     __shared__ double tot[NV * kMaxRhs];
+    __shared__ double scratch[256];
     __shared__ bool is_last;
-    const int n = 1 << rhs_log2;
+    const int n = 1 << rhs_log2, P = NV * n;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const unsigned nb = gridDim.x, G = red_group_size(nb, P), ng = (nb + G - 1) / G, grp = blockIdx.x / G;
+    const unsigned gsize = nb - grp * G < G ? nb - grp * G : G;
     if (lane < n)
 #pragma unroll
         for (int k = 0; k < NV; ++k) sw[k][warp][lane] = v[k];
     __syncthreads();
-    if (threadIdx.x < NV * n) {
+    if ((int)threadIdx.x < P) {
         const int k = threadIdx.x / n, r = threadIdx.x % n;
         double b = 0.0;
         for (int w = 0; w < nw; ++w) b += sw[k][w][r];
-        red.partials[((size_t)k * n + r) * gridDim.x + blockIdx.x] = b;
+        red.partials[((size_t)k * n + r) * nb + blockIdx.x] = b;
         __threadfence();
     }
     __syncthreads();
-    if (threadIdx.x == 0) is_last = atomicAdd(red.counter, 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) is_last = atomicAdd(red.counter + 1 + grp, 1u) == gsize - 1;
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    // one warp per (value, rhs): lane-strided sums, then a fixed shuffle tree
-    for (int q = warp; q < NV * n; q += nw) {
-        double a = 0.0;
-        for (int b = lane; b < (int)gridDim.x; b += 32) a += __ldcg(red.partials + (size_t)q * gridDim.x + b);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
-        if (lane == 0) tot[q] = a;
+    // the last block of the group: the group's partials in block order
+    block_row_sums(red.partials + (size_t)grp * G, nb, P, gsize, tot, scratch);
+    if (ng > 1) {
+        double *gsum = red.partials + (size_t)P * nb;
+        if ((int)threadIdx.x < P) {
+            gsum[(size_t)threadIdx.x * ng + grp] = tot[threadIdx.x];
+            __threadfence();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            red.counter[1 + grp] = 0u;
+            is_last = atomicAdd(red.counter, 1u) == ng - 1;
+        }
+        __syncthreads();
+        if (!is_last) return;
+        __threadfence();
+        // the last group: the group sums in group order
+        block_row_sums(gsum, ng, P, ng, tot, scratch);
     }
-    __syncthreads();
     if (threadIdx.x == 0) {
+        red.counter[1] = 0u;  // (one group: its ticket; otherwise already reset)
         if (kind == FIN_STORE) {
             for (int q = 0; q < NV * n; ++q) out[q] = tot[q];
         } else {

@@ -65,9 +65,13 @@ cudaError_t launch_cg_true_residual(const FieldView &rhs, const FieldView &q, co
 cudaError_t launch_cg_ctrl_reliable(const CgState *st, cudaGraphConditionalHandle h, cudaStream_t s);
 cudaError_t launch_cg_ctrl_loop(CgState *st, cudaGraphConditionalHandle h, cudaStream_t s);
 
-// Copy between one rhs of a batched field and a plain field of the same
-// precision and halves: to_batch = 1 copies plain -> batched[rhs].
-cudaError_t launch_batch_copy(const FieldView &batched, const FieldView &plain, int rhs, int to_batch, cudaStream_t s);
+// Copy between rhs 0..n-1 of a batched field and n plain fields of the same
+// precision and halves, in one launch: to_batch = 1 copies plain[k] ->
+// batched[rhs k] (other rhs untouched).
+struct PlainSet {
+    FieldView f[kMaxRhs];
+};
+cudaError_t launch_batch_copy(const FieldView &batched, const FieldView *plain, int n, int to_batch, cudaStream_t s);
 
 // Staggered hopping term (csrc/staggered.cu).  in/out indexed by output
 // parity as for DslashLaunch; staggered fields hold 3 complex per site.

@@ -85,6 +85,24 @@ void coef_block(double *t, bool eo, double kappa, double a)
     memcpy(t + kCoefTwistInv, ti.c, 4 * sizeof(double));
 }
 
+// The reliable-update factor for reliable_delta = 0.  Between two FP64
+// updates the inner iteration reduces the residual by 1/delta; its drift
+// from the true residual grows with the inner format's rounding unit u, so
+// delta stays well above u: about 20 u for FP16 (u = 2^-11); 1e-3 for FP32
+// and 1e-4 for DF64, far above theirs; 0.1 for BF16 (u = 2^-8), which needed
+// more iterations at 0.01 and stalled at 0.003.  Measured on the 24^3x8,
+// 32^3x8 and 48^3x12 workloads: FP16 at 0.01 takes 5 updates instead of 9
+// at 0.1 with the same iteration count (48^3x12: 33.0 ms against 42.7 ms).
+double default_reliable_delta(int inner_prec)
+{
+    switch (inner_prec) {
+    case QCD_PREC_F32: return 1e-3;
+    case QCD_PREC_F16: return 1e-2;
+    case QCD_PREC_DF64: return 1e-4;
+    default: return 0.1;
+    }
+}
+
 // A hop whose epilogue coefficients come from block `off` of the table.
 HopArgs table_hop(const OpCtx &c, int off)
 {
@@ -511,8 +529,8 @@ qcd_status qcd::solve_impl(const qcd_gauge *g, qcd_spinor *const *x, const qcd_s
     const bool mixed = prm->inner_prec != QCD_PREC_F64;
     if (mixed && prm->inner_recon != 18 && prm->inner_recon != 12 && prm->inner_recon != 8)
         return fail(QCD_ERR_INVALID_ARG, "solve_cg: bad inner_recon");
-    if (mixed && !(prm->reliable_delta > 0.0 && prm->reliable_delta < 1.0))
-        return fail(QCD_ERR_INVALID_ARG, "solve_cg: reliable_delta must be in (0, 1)");
+    if (mixed && !(prm->reliable_delta >= 0.0 && prm->reliable_delta < 1.0))
+        return fail(QCD_ERR_INVALID_ARG, "solve_cg: reliable_delta must be 0 (by inner precision) or in (0, 1)");
 
     const int sp = prm->inner_prec;
     // DF64 links are kept at 18 reals (rebuilding a row in double-float
@@ -542,12 +560,15 @@ qcd_status qcd::solve_impl(const qcd_gauge *g, qcd_spinor *const *x, const qcd_s
         xf = ws_field(lat, "cg_xx", 2, QCD_PREC_F64, L);
         if (!bf.hv[0].data || !xf.hv[0].data) return fail(QCD_ERR_OOM, "solve_cg: workspace");
         QCD_TRY(launch_zero(bf, s), "solve_cg: gather");  // padding right-hand sides are zero (solved at once)
-        for (int k = 0; k < nrhs; ++k) QCD_TRY(launch_batch_copy(bf, view_of(b[k]), k, 1, s), "solve_cg: gather");
+        FieldView bv[kMaxRhs];
+        for (int k = 0; k < nrhs; ++k) bv[k] = view_of(b[k]);
+        QCD_TRY(launch_batch_copy(bf, bv, nrhs, 1, s), "solve_cg: gather");
     }
     // reduction scratch: NV (<= 2) x N partials per block of the largest grid
     Reduction red = reduction_of(lat);
     if (N > 1) {
-        const size_t need = 2 * (size_t)N * (((size_t)2 * (lat->h << L) + 63) / 64 + 64);
+        const size_t bmax = ((size_t)2 * (lat->h << L) + 63) / 64;
+        const size_t need = std::max(red_partials_needed(2 * (size_t)N, bmax), red_partials_needed(N, bmax));
         red.partials = static_cast<double *>(workspace(lat, "cg_partials", need * sizeof(double)));
         red.cap = need;
         if (!red.partials) return fail(QCD_ERR_OOM, "solve_cg: workspace");
@@ -660,7 +681,7 @@ qcd_status qcd::solve_impl(const qcd_gauge *g, qcd_spinor *const *x, const qcd_s
     }
     CgFields F{c, Uh, Us, g->recon, srecon, mixed, rhs, xh, rh, qh, th, sh, rs, ps, qs, ts, ss, xs, red, lat->state,
                split, c.eo ? bp : bf, Um, srecon, mid, rho_m, t_m, r_m};
-    const double delta = mixed ? prm->reliable_delta : 0.0;
+    const double delta = !mixed ? 0.0 : prm->reliable_delta > 0.0 ? prm->reliable_delta : default_reliable_delta(sp);
     RhsValues tol2{};
     for (int k = 0; k < kMaxRhs; ++k) tol2.v[k] = prm[k < nrhs ? k : 0].tol * prm[k < nrhs ? k : 0].tol;
     QCD_TRY(launch_cg_state_init(lat->state, N, tol2, delta * delta, prm->maxiter, s), "solve_cg: init");
@@ -733,8 +754,11 @@ after_loop:
     QCD_TRY(launch_diff_norm2(*chk, bf, F.red, lat->red_out_big, s), "solve_cg: residual");
     QCD_TRY(cudaMemcpyAsync(r2.data(), lat->red_out_big, 2 * N * sizeof(double), cudaMemcpyDeviceToHost, s),
             "solve_cg: residual");
-    if (N > 1)
-        for (int k = 0; k < nrhs; ++k) QCD_TRY(launch_batch_copy(xf, view_of(x[k]), k, 0, s), "solve_cg: scatter");
+    if (N > 1) {
+        FieldView xv[kMaxRhs];
+        for (int k = 0; k < nrhs; ++k) xv[k] = view_of(x[k]);
+        QCD_TRY(launch_batch_copy(xf, xv, nrhs, 0, s), "solve_cg: scatter");
+    }
     QCD_TRY(cudaStreamSynchronize(s), "solve_cg: residual");
     for (int k = 0; k < N; ++k) full_rel[k] = r2[N + k] > 0 ? std::sqrt(r2[k] / r2[N + k]) : 0.0;
 

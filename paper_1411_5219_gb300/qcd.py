@@ -336,7 +336,7 @@ def apply_dslash_multi(gauge: Gauge, outs, ins, dagger: bool = False, stream=Non
 
 def solve_cg_multi(gauge: Gauge, xs, bs, kappa: float, mu: float = 0.0, tol: float = 1e-10, maxiter: int = 20000,
                    eo: bool = True, normal: bool = False, inner_prec: str = "f64", inner_recon: int = 12,
-                   reliable_delta: float = 0.1, stream=None, raise_on_error: bool = True):
+                   reliable_delta: float = 0.0, stream=None, raise_on_error: bool = True):
     """Batched CG over len(bs) systems (qcd_solve_cg_multi); returns (status, [stats dict])."""
     if len(xs) != len(bs):
         raise ValueError("xs and bs differ in length")
@@ -352,7 +352,7 @@ def solve_cg_multi(gauge: Gauge, xs, bs, kappa: float, mu: float = 0.0, tol: flo
 
 
 def solve_cg_batch(gauge: Gauge, xs, bs, kappas, mus=None, tols=None, maxiter: int = 20000, eo: bool = True,
-                   normal: bool = False, inner_prec: str = "f64", inner_recon: int = 12, reliable_delta: float = 0.1,
+                   normal: bool = False, inner_prec: str = "f64", inner_recon: int = 12, reliable_delta: float = 0.0,
                    stream=None, raise_on_error: bool = True):
     """Batched CG over systems with their own kappa, mu and tol (qcd_solve_cg_batch);
     returns (status, [stats dict])."""
@@ -411,7 +411,7 @@ def solve_cg_many(gauges, xs, bs, kappas, mus=None, tols=None, maxiter: int = 20
 
 def solve_cg(gauge: Gauge, x: Spinor, b: Spinor, kappa: float, mu: float = 0.0, tol: float = 1e-10,
              maxiter: int = 20000, eo: bool = True, normal: bool = False, inner_prec: str = "f64",
-             inner_recon: int = 12, reliable_delta: float = 0.1, stream=None, raise_on_error: bool = True):
+             inner_recon: int = 12, reliable_delta: float = 0.0, stream=None, raise_on_error: bool = True):
     """CG solve (see qcd_solve_cg); returns (status, stats dict)."""
     prm = SolverParams(float(kappa), float(mu), float(tol), int(maxiter), int(bool(eo)), int(bool(normal)),
                        PREC[inner_prec], int(inner_recon), float(reliable_delta))
@@ -484,7 +484,7 @@ class Server:
 
     def submit(self, gauge_id: int, b_host, x_host, kappa: float, mu: float = 0.0, tol: float = 1e-10,
                maxiter: int = 20000, inner_prec: str = "f16", inner_recon: int = 12,
-               reliable_delta: float = 0.1) -> int:
+               reliable_delta: float = 0.0) -> int:
         req = Request(int(gauge_id), float(kappa), float(mu), float(tol), int(maxiter), PREC[inner_prec],
                       int(inner_recon), float(reliable_delta), _host_ptr(b_host), _host_ptr(x_host))
         rid = ctypes.c_longlong()

@@ -340,6 +340,31 @@ def test_solve_eo_matches_oracle(q, inner, kappa, mu):
         assert st["reliable_updates"] >= 1
 
 
+@pytest.mark.parametrize("inner", ["f32", "f16", "bf16"])
+def test_reliable_delta_default_by_precision(q, inner):
+    """reliable_delta = 0 picks the factor from the inner precision (FP32
+    1e-3, FP16 1e-2, BF16 0.1): no more FP64 updates than at 0.1, the same
+    target met, and the solution the oracle's; values outside [0, 1) fail."""
+    dims = (8, 8, 8, 4)
+    lat, U, g = gauge(q, dims, eps=0.2, seed=77)
+    b = syn.gaussian_spinor(dims, 81)
+    bs = q.Spinor(lat, "full", "f64")
+    bs.upload(b)
+    res = {}
+    for delta in (0.0, 0.1):
+        x = q.Spinor(lat, "full", "f64")
+        status, st = q.solve_cg(g, x, bs, 0.155, 0.01, tol=1e-10, inner_prec=inner, reliable_delta=delta)
+        assert status == 0, (delta, st)
+        assert schur_residual_oracle(U, b, x.download(), 0.155, 0.01) <= 1.5e-10
+        res[delta] = st["reliable_updates"]
+    assert res[0.0] <= res[0.1], res
+    if inner != "bf16":
+        assert res[0.0] < res[0.1], res
+    for bad in (1.0, -0.1):
+        with pytest.raises(q.QcdError):
+            q.solve_cg(g, q.Spinor(lat, "full", "f64"), bs, 0.155, tol=1e-10, inner_prec=inner, reliable_delta=bad)
+
+
 @pytest.mark.parametrize("inner", ["f16", "bf16", "f32"])
 @pytest.mark.parametrize("kappa", [0.12, 0.125, 0.13])
 def test_solve_mixed_near_critical_kappa(q, inner, kappa):
