@@ -47,7 +47,7 @@ HBM_FALLBACK_GBS = 6800.0
 # DRAM bytes (read + write) of one FP64 D_eo launch at 24^3 x 8 from an ncu
 # capture of the current kernel;
 # set to None when the kernel changes.
-TRAFFIC_F64_D_24 = 76.38e6
+TRAFFIC_F64_D_24 = 76.44e6
 
 
 def workload_config():
