@@ -283,7 +283,12 @@ __global__ void __launch_bounds__(TPB, kMinBlocks) dslash_kernel(const DslashLau
     const int ne = a.g.h << a.rhs_log2;
     const int nbp = (ne + TPB - 1) / TPB;
     const int p = a.both ? (int)(blockIdx.x >= (unsigned)nbp) : a.out_parity;
-    const int e = (blockIdx.x - (a.both ? p * nbp : 0)) * blockDim.x + threadIdx.x;
+    int bl = blockIdx.x - (a.both ? p * nbp : 0);
+    // with tmap = blocks per time slice, consecutive blocks take the same
+    // space chunk at consecutive t, so every neighbour is re-read within a
+    // few MB of traffic (an L2 hit) even when a batched field exceeds L2
+    if (a.tmap) bl = (bl % a.g.L[3]) * a.tmap + bl / a.g.L[3];
+    const int e = bl * blockDim.x + threadIdx.x;
     const int L = a.rhs_log2, rhs = e & ((1 << L) - 1);
     const int i = e >> L;
     // fused norm: summed within the warp in float by the FP32/16-bit kernels

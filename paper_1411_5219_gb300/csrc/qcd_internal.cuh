@@ -1186,6 +1186,7 @@ struct DslashLaunch {
     int rhs_log2;       // batched fields: element = site * 2^rhs_log2 + rhs
     int tpb;            // threads per block (FP32/16-bit kernels; 0: default)
     int split;          // threads per output site: 1 (0), or 8 (FP64 reconstruct-18, one rhs)
+    int tmap;           // 0, or blocks per time slice: blocks run in t-major order (batched fields)
     int dagger;
     GaugeView U;
     SpinorView in[2], out[2], y[2];
