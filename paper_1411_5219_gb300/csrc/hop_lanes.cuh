@@ -87,9 +87,9 @@ __device__ __forceinline__ void hop_lane8(const Geom &g, const double2 *U, int u
             const double2 v = __ldg(up + (size_t)(bwd ? 3 * b + a : 3 * a + b) * ustride);
             m[a][b] = bwd ? mk(v.x, -v.y) : mk(v.x, v.y);
         }
-    // projector sign: (1 - S gamma) forward, (1 + S gamma) backward; S = -1 for D^dagger
-    const double sgn = (dagger ? -1.0 : 1.0) * (bwd ? -1.0 : 1.0);
-    const bool sneg = sgn < 0.0;
+    // projector sign: (1 - S gamma) forward, (1 + S gamma) backward; S = -1
+    // for D^dagger (a negative product when exactly one of the two holds)
+    const bool sneg = dagger != bwd;
     // h_s = psi_s - S B[s][col] psi_{2 + col}
     cx<double> h[2][3];
 #pragma unroll
