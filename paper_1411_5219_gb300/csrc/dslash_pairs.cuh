@@ -83,6 +83,13 @@ struct PairSrc<SpF32> {
 // Spin projection of a fetched spinor (16-bit ones unscaled) straight from
 // its storage: lane 0 is h_0 = psi_0 + ..., lane 1 is h_1 = psi_1 + ...; the
 // lower spins enter in the order (3, 2) for x and y, (2, 3) for z and t.
+template <typename SF>
+struct is_fp16_spinor : std::false_type {};
+template <bool N>
+struct is_fp16_spinor<Sp16<__half, N>> : std::true_type {};
+
+__device__ __forceinline__ __half2 as_h2(uint32_t w) { return *reinterpret_cast<__half2 *>(&w); }
+
 template <typename SF, int MU, int S>
 __device__ __forceinline__ HalfPairs project_pairs(const typename SF::Raw &w)
 {
@@ -90,6 +97,38 @@ __device__ __forceinline__ HalfPairs project_pairs(const typename SF::Raw &w)
     constexpr int b0 = MU <= 1 ? 3 : 2, b1 = MU <= 1 ? 2 : 3;
     constexpr float s = (float)S;
     HalfPairs h;
+    if constexpr (is_fp16_spinor<SF>::value) {
+        // FP16: the projection in half2 arithmetic on the (re, im) words, then
+        // 12 conversions to FP32 instead of 24 (the conversions run on the
+        // FMA pipe, the kernel's busiest unit).  h is rounded to FP16 once
+        // more (half an FP16 unit of |h|, within the storage tolerance).
+        const __half2 pp = __floats2half2_rn(s, s), mm = __floats2half2_rn(-s, -s);
+        const __half2 mp = __floats2half2_rn(-s, s), pm = __floats2half2_rn(s, -s);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            using H = typename SF::H16;
+            const __half2 a0 = as_h2(word16<H>(w.w, c)), a1 = as_h2(word16<H>(w.w, 3 + c));
+            const __half2 x0 = as_h2(word16<H>(w.w, 3 * b0 + c)), x1 = as_h2(word16<H>(w.w, 3 * b1 + c));
+            __half2 h0, h1;
+            if (MU == 0) {  // (psi0 + S i psi3, psi1 + S i psi2); i z = (-im, re)
+                h0 = __hfma2(__lowhigh2highlow(x0), mp, a0);
+                h1 = __hfma2(__lowhigh2highlow(x1), mp, a1);
+            } else if (MU == 1) {  // (psi0 + S psi3, psi1 - S psi2)
+                h0 = __hfma2(x0, pp, a0);
+                h1 = __hfma2(x1, mm, a1);
+            } else if (MU == 2) {  // (psi0 + S i psi2, psi1 - S i psi3)
+                h0 = __hfma2(__lowhigh2highlow(x0), mp, a0);
+                h1 = __hfma2(__lowhigh2highlow(x1), pm, a1);
+            } else {  // (psi0 - S psi2, psi1 - S psi3)
+                h0 = __hfma2(x0, mm, a0);
+                h1 = __hfma2(x1, mm, a1);
+            }
+            const float2 f0 = __half22float2(h0), f1 = __half22float2(h1);
+            h.r[c] = make_float2(f0.x, f1.x);
+            h.i[c] = make_float2(f0.y, f1.y);
+        }
+        return h;
+    }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const int a0 = c, a1 = 3 + c, x0 = 3 * b0 + c, x1 = 3 * b1 + c;

@@ -109,6 +109,24 @@ def test_norm2_matches_numpy(q):
     assert abs(s.norm2() - np.vdot(psi, psi).real) < 1e-12 * np.vdot(psi, psi).real
 
 
+@pytest.mark.parametrize("dims", [(6, 4, 2, 8), (24, 24, 24, 24), (48, 48, 48, 12)])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_norm2_one_and_two_level_reductions(q, dims, prec):
+    """The grid reduction in one level (a few blocks) and in two (2592 and
+    10,368 blocks of 128: groups of 2048 blocks, then the group sums), against
+    numpy on the stored values."""
+    lat = q.Lattice(dims, -1)
+    rng = np.random.default_rng(1401)
+    psi = (rng.standard_normal(dims[::-1] + (4, 3)) + 1j * rng.standard_normal(dims[::-1] + (4, 3)))
+    if prec == "f32":
+        psi = psi.astype(np.complex64).astype(np.complex128)
+    s = q.Spinor(lat, "full", prec)
+    s.upload(psi)
+    want = float(np.vdot(psi, psi).real)
+    # FP32 fields: each site's 24 squares are summed in float before the FP64 reduction
+    assert abs(s.norm2() - want) <= (1e-13 if prec == "f64" else 2e-7) * want
+
+
 # -------------------------------------------------------------------- Dslash
 
 @pytest.mark.parametrize("dims", DIMS)
@@ -193,8 +211,9 @@ def _stored_links_recon12(U, prec):
 def test_low_precision_bound_from_storage_rounding(q, prec):
     """The 8u tolerance of the 16-bit tests, taken apart: a model that rounds
     the inputs as the storage does and then computes exactly is within 2u of
-    the GPU result (the output rounding and FP32 arithmetic), and within 6u of
-    the exact result (the input and link roundings)."""
+    the GPU result (the output rounding, FP32 arithmetic and, for FP16, the
+    FP16 rounding of each projected half spinor), and within 6u of the exact
+    result (the input and link roundings)."""
     dims = (8, 6, 4, 10)
     lat, U, g = gauge(q, dims, recon=12)
     half_in = syn.to_half(syn.gaussian_spinor(dims, 13), 1)
