@@ -318,10 +318,9 @@ qcd_status qcd_solve_cg_batch(const qcd_gauge *g, qcd_spinor *const *x, const qc
  * bitwise the same alone and in any batch.  max_blocks (0: as many as fit
  * the GPU at once, else at least n) caps the grid, so a caller that shares
  * the GPU with other work does not wait for all of it to be free: a
- * cooperative launch starts only once every block is resident.  wait_cycles
- * bounds every
- * barrier wait (0: about two seconds); when a wait runs out the call
- * returns QCD_ERR_TIMEOUT and the context stays usable.  The systems' lattice
+ * cooperative launch starts only once every block is resident.
+ * wait_cycles bounds every barrier wait (0: about two seconds); when a wait
+ * runs out the call returns QCD_ERR_TIMEOUT and the context stays usable.  The systems' lattice
  * handles hold the scratch fields, so calls that share a lattice must not
  * overlap on the device.  Synchronous (returns after the stats are final);
  * errors as for qcd_solve_cg, per system in stats. */
@@ -377,11 +376,14 @@ typedef struct qcd_server qcd_server;
 typedef struct {
     int slots;             /* concurrent solves (1..64) */
     size_t memory_budget;  /* device bytes the solver contexts may use */
-    int batch_small_sites; /* 0: off; else requests on lattices of at most this
-                              many sites that are queued together (up to 16,
-                              same maxiter) run as one qcd_solve_cg_many launch
-                              (FP64 CG, which is faster than a mixed solve at
-                              such volumes; the same 1e-10-type target) */
+    int batch_small_sites; /* 0 (default): off; else requests on lattices of at
+                              most this many sites that are queued together
+                              (up to 16, same maxiter) run as one
+                              qcd_solve_cg_many launch (FP64 CG to each
+                              request's tolerance).  A cooperative launch
+                              waits for, then holds, the SMs other slots'
+                              solves want, so it pays only when small
+                              requests dominate the stream. */
 } qcd_server_config;
 typedef struct {
     int gauge_id;          /* from qcd_server_add_gauge */
