@@ -90,6 +90,37 @@ struct is_fp16_spinor<Sp16<__half, N>> : std::true_type {};
 
 __device__ __forceinline__ __half2 as_h2(uint32_t w) { return *reinterpret_cast<__half2 *>(&w); }
 
+// FP16 spinors: the spin projection in half2 arithmetic on the stored (re,
+// im) words: hw[s][c] = h_s of colour c as a half2 word.  h is rounded to
+// FP16 once more (half an FP16 unit of |h|, within the storage tolerance).
+template <typename SF, int MU, int S>
+__device__ __forceinline__ void project_words(const typename SF::Raw &w, __half2 (&hw)[2][3])
+{
+    using H = typename SF::H16;
+    constexpr int b0 = MU <= 1 ? 3 : 2, b1 = MU <= 1 ? 2 : 3;
+    constexpr float s = (float)S;
+    const __half2 pp = __floats2half2_rn(s, s), mm = __floats2half2_rn(-s, -s);
+    const __half2 mp = __floats2half2_rn(-s, s), pm = __floats2half2_rn(s, -s);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const __half2 a0 = as_h2(word16<H>(w.w, c)), a1 = as_h2(word16<H>(w.w, 3 + c));
+        const __half2 x0 = as_h2(word16<H>(w.w, 3 * b0 + c)), x1 = as_h2(word16<H>(w.w, 3 * b1 + c));
+        if (MU == 0) {  // (psi0 + S i psi3, psi1 + S i psi2); i z = (-im, re)
+            hw[0][c] = __hfma2(__lowhigh2highlow(x0), mp, a0);
+            hw[1][c] = __hfma2(__lowhigh2highlow(x1), mp, a1);
+        } else if (MU == 1) {  // (psi0 + S psi3, psi1 - S psi2)
+            hw[0][c] = __hfma2(x0, pp, a0);
+            hw[1][c] = __hfma2(x1, mm, a1);
+        } else if (MU == 2) {  // (psi0 + S i psi2, psi1 - S i psi3)
+            hw[0][c] = __hfma2(__lowhigh2highlow(x0), mp, a0);
+            hw[1][c] = __hfma2(__lowhigh2highlow(x1), pm, a1);
+        } else {  // (psi0 - S psi2, psi1 - S psi3)
+            hw[0][c] = __hfma2(x0, mm, a0);
+            hw[1][c] = __hfma2(x1, mm, a1);
+        }
+    }
+}
+
 template <typename SF, int MU, int S>
 __device__ __forceinline__ HalfPairs project_pairs(const typename SF::Raw &w)
 {
@@ -98,54 +129,34 @@ __device__ __forceinline__ HalfPairs project_pairs(const typename SF::Raw &w)
     constexpr float s = (float)S;
     HalfPairs h;
     if constexpr (is_fp16_spinor<SF>::value) {
-        // FP16: the projection in half2 arithmetic on the (re, im) words, then
-        // 12 conversions to FP32 instead of 24 (the conversions run on the
-        // FMA pipe, the kernel's busiest unit).  h is rounded to FP16 once
-        // more (half an FP16 unit of |h|, within the storage tolerance).
-        const __half2 pp = __floats2half2_rn(s, s), mm = __floats2half2_rn(-s, -s);
-        const __half2 mp = __floats2half2_rn(-s, s), pm = __floats2half2_rn(s, -s);
+        // 12 conversions to FP32 instead of 24 (they run on the FMA pipe)
+        __half2 hw[2][3];
+        project_words<SF, MU, S>(w, hw);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            using H = typename SF::H16;
-            const __half2 a0 = as_h2(word16<H>(w.w, c)), a1 = as_h2(word16<H>(w.w, 3 + c));
-            const __half2 x0 = as_h2(word16<H>(w.w, 3 * b0 + c)), x1 = as_h2(word16<H>(w.w, 3 * b1 + c));
-            __half2 h0, h1;
-            if (MU == 0) {  // (psi0 + S i psi3, psi1 + S i psi2); i z = (-im, re)
-                h0 = __hfma2(__lowhigh2highlow(x0), mp, a0);
-                h1 = __hfma2(__lowhigh2highlow(x1), mp, a1);
-            } else if (MU == 1) {  // (psi0 + S psi3, psi1 - S psi2)
-                h0 = __hfma2(x0, pp, a0);
-                h1 = __hfma2(x1, mm, a1);
-            } else if (MU == 2) {  // (psi0 + S i psi2, psi1 - S i psi3)
-                h0 = __hfma2(__lowhigh2highlow(x0), mp, a0);
-                h1 = __hfma2(__lowhigh2highlow(x1), pm, a1);
-            } else {  // (psi0 - S psi2, psi1 - S psi3)
-                h0 = __hfma2(x0, mm, a0);
-                h1 = __hfma2(x1, mm, a1);
-            }
-            const float2 f0 = __half22float2(h0), f1 = __half22float2(h1);
+            const float2 f0 = __half22float2(hw[0][c]), f1 = __half22float2(hw[1][c]);
             h.r[c] = make_float2(f0.x, f1.x);
             h.i[c] = make_float2(f0.y, f1.y);
         }
-        return h;
-    }
+    } else {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const int a0 = c, a1 = 3 + c, x0 = 3 * b0 + c, x1 = 3 * b1 + c;
-        const float2 ar = make_float2(P::re(w, a0), P::re(w, a1)), ai = make_float2(P::im(w, a0), P::im(w, a1));
-        const float2 xr = make_float2(P::re(w, x0), P::re(w, x1)), xi = make_float2(P::im(w, x0), P::im(w, x1));
-        if (MU == 0) {  // h = (psi0 + S i psi3, psi1 + S i psi2)
-            h.r[c] = fma2(xi, make_float2(-s, -s), ar);
-            h.i[c] = fma2(xr, make_float2(s, s), ai);
-        } else if (MU == 1) {  // h = (psi0 + S psi3, psi1 - S psi2)
-            h.r[c] = fma2(xr, make_float2(s, -s), ar);
-            h.i[c] = fma2(xi, make_float2(s, -s), ai);
-        } else if (MU == 2) {  // h = (psi0 + S i psi2, psi1 - S i psi3)
-            h.r[c] = fma2(xi, make_float2(-s, s), ar);
-            h.i[c] = fma2(xr, make_float2(s, -s), ai);
-        } else {  // h = (psi0 - S psi2, psi1 - S psi3)
-            h.r[c] = fma2(xr, make_float2(-s, -s), ar);
-            h.i[c] = fma2(xi, make_float2(-s, -s), ai);
+        for (int c = 0; c < 3; ++c) {
+            const int a0 = c, a1 = 3 + c, x0 = 3 * b0 + c, x1 = 3 * b1 + c;
+            const float2 ar = make_float2(P::re(w, a0), P::re(w, a1)), ai = make_float2(P::im(w, a0), P::im(w, a1));
+            const float2 xr = make_float2(P::re(w, x0), P::re(w, x1)), xi = make_float2(P::im(w, x0), P::im(w, x1));
+            if (MU == 0) {  // h = (psi0 + S i psi3, psi1 + S i psi2)
+                h.r[c] = fma2(xi, make_float2(-s, -s), ar);
+                h.i[c] = fma2(xr, make_float2(s, s), ai);
+            } else if (MU == 1) {  // h = (psi0 + S psi3, psi1 - S psi2)
+                h.r[c] = fma2(xr, make_float2(s, -s), ar);
+                h.i[c] = fma2(xi, make_float2(s, -s), ai);
+            } else if (MU == 2) {  // h = (psi0 + S i psi2, psi1 - S i psi3)
+                h.r[c] = fma2(xi, make_float2(-s, s), ar);
+                h.i[c] = fma2(xr, make_float2(s, -s), ai);
+            } else {  // h = (psi0 - S psi2, psi1 - S psi3)
+                h.r[c] = fma2(xr, make_float2(-s, -s), ar);
+                h.i[c] = fma2(xi, make_float2(-s, -s), ai);
+            }
         }
     }
     return h;
@@ -237,6 +248,124 @@ __device__ __forceinline__ void accumulate_pairs(AccPairs &acc, const HalfPairs 
     }
 }
 
+// ---- FP16 spinors with FP16 links (reconstruct 12 or 18): the SU(3)
+// product by mixed-precision FMA (fma.rn.f32.f16: an FP16 x FP16 product,
+// exact in FP32, added to an FP32 value) straight from the stored link words
+// and the half2-projected half spinor, so neither needs converting to FP32
+// and no link entry is copied into both lanes of a pair.  Measured on
+// GB300: the mixed FMA issues at the FFMA rate, and with operands taken from
+// the halves of 32-bit words it ran 25 % above conversions plus packed FMAs.
+
+template <typename GF>
+struct is_fp16_links : std::false_type {};
+template <>
+struct is_fp16_links<G16<__half, 12>> : std::true_type {};
+template <>
+struct is_fp16_links<G16<__half, 18>> : std::true_type {};
+
+// the (re, im) halves of a half2 word as 16-bit registers
+__device__ __forceinline__ void halves(__half2 w, unsigned short &re, unsigned short &im)
+{
+    const uint32_t u = *reinterpret_cast<uint32_t *>(&w);
+    asm("mov.b32 {%0, %1}, %2;" : "=h"(re), "=h"(im) : "r"(u));
+}
+
+__device__ __forceinline__ float fmah(unsigned short a, unsigned short b, float c)
+{
+    float d;
+    asm("fma.rn.f32.f16 %0, %1, %2, %3;" : "=f"(d) : "h"(a), "h"(b), "f"(c));
+    return d;
+}
+
+__device__ __forceinline__ __half2 neg_im(__half2 w) { return __hmul2(w, __floats2half2_rn(1.0f, -1.0f)); }
+__device__ __forceinline__ __half2 neg_re(__half2 w) { return __hmul2(w, __floats2half2_rn(-1.0f, 1.0f)); }
+
+// U (kAdj false) or U^dagger (kAdj true) times the two half-spinor spins,
+// from the link's half2 words (u[row][col]), into FP32 pairs.
+template <bool kAdj>
+__device__ __forceinline__ HalfPairs su3_mixed(const __half2 (&u)[3][3], const __half2 (&hw)[2][3])
+{
+    // re and im halves of h, and of h with one part negated (the minus signs
+    // of the complex products)
+    unsigned short hr[2][3], hi[2][3], hn[2][3];
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            unsigned short r_, i_, nr_, ni_;
+            halves(hw[s][b], r_, i_);
+            halves(kAdj ? neg_re(hw[s][b]) : neg_im(hw[s][b]), nr_, ni_);
+            hr[s][b] = r_;
+            hi[s][b] = i_;
+            hn[s][b] = kAdj ? nr_ : ni_;  // -Re h (adjoint) or -Im h
+        }
+    HalfPairs v;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float re[2], im[2];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            float r_ = 0.0f, i_ = 0.0f;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                unsigned short ur, ui;
+                halves(kAdj ? u[b][a] : u[a][b], ur, ui);
+                if (!kAdj) {  // Re += ur hr - ui hi ; Im += ur hi + ui hr
+                    r_ = fmah(ur, hr[s][b], r_);
+                    r_ = fmah(ui, hn[s][b], r_);
+                    i_ = fmah(ur, hi[s][b], i_);
+                    i_ = fmah(ui, hr[s][b], i_);
+                } else {  // conj(U_ba) h: Re += ur hr + ui hi ; Im += ur hi - ui hr
+                    r_ = fmah(ur, hr[s][b], r_);
+                    r_ = fmah(ui, hi[s][b], r_);
+                    i_ = fmah(ur, hi[s][b], i_);
+                    i_ = fmah(ui, hn[s][b], i_);
+                }
+            }
+            re[s] = r_;
+            im[s] = i_;
+        }
+        v.r[a] = make_float2(re[0], re[1]);
+        v.i[a] = make_float2(im[0], im[1]);
+    }
+    return v;
+}
+
+// The link as half2 words; reconstruct-12 rebuilds row 2 = conj(row 0 x
+// row 1) from the stored FP16 rows with exact products and FP32 sums, and
+// rounds it to FP16 (half an FP16 unit per entry).
+template <typename GF>
+__device__ __forceinline__ void link_words(const typename GF::Raw &r, __half2 (&u)[3][3])
+{
+#pragma unroll
+    for (int k = 0; k < GF::kRecon_ / 2; ++k) u[k / 3][k % 3] = as_h2(r.w[k]);
+    if constexpr (GF::kRecon_ == 12) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int a = (c + 1) % 3, b = (c + 2) % 3;
+            // P = U0a U1b - U0b U1a ; row 2 = conj(P)
+            unsigned short ar, ai, br, bi, cr, ci, dr, di, nar, nai, ncr, nci;
+            halves(u[0][a], ar, ai);
+            halves(u[1][b], br, bi);
+            halves(u[0][b], cr, ci);
+            halves(u[1][a], dr, di);
+            halves(__hneg2(u[0][a]), nar, nai);
+            halves(__hneg2(u[0][b]), ncr, nci);
+            // Re P = ar br - ai bi - cr dr + ci di
+            float re = fmah(ar, br, 0.0f);
+            re = fmah(nai, bi, re);
+            re = fmah(ncr, dr, re);
+            re = fmah(ci, di, re);
+            // -Im P = -(ar bi + ai br) + cr di + ci dr
+            float mi = fmah(nar, bi, 0.0f);
+            mi = fmah(nai, br, mi);
+            mi = fmah(cr, di, mi);
+            mi = fmah(ci, dr, mi);
+            u[2][c] = __floats2half2_rn(re, mi);
+        }
+    }
+}
+
 // One hop of a 16-bit spinor: project, multiply, rebuild and accumulate;
 // `flip` applies the boundary factor -1 (folded into the weight with the
 // FP16 per-site scale).
@@ -244,8 +373,16 @@ template <typename SF, typename GF, int MU, int S, bool kAdj, bool kFirst>
 __device__ __forceinline__ void hop_pairs(AccPairs &acc, const typename SF::Raw &rs, const typename GF::Raw &ru,
                                           bool flip)
 {
-    const HalfPairs h = project_pairs<SF, MU, S>(rs);
-    const HalfPairs v = su3_pairs<kAdj>(GF::decode(ru), h);
+    HalfPairs v;
+    if constexpr (is_fp16_spinor<SF>::value && is_fp16_links<GF>::value) {
+        __half2 hw[2][3], u[3][3];
+        project_words<SF, MU, S>(rs, hw);
+        link_words<GF>(ru, u);
+        v = su3_mixed<kAdj>(u, hw);
+    } else {
+        const HalfPairs h = project_pairs<SF, MU, S>(rs);
+        v = su3_pairs<kAdj>(GF::decode(ru), h);
+    }
     const float sc = SF::scale(rs);
     accumulate_pairs<MU, S, kFirst>(acc, v, flip ? -sc : sc);
 }
