@@ -262,13 +262,18 @@ __host__ __device__ constexpr int dslash_min_blocks()
 }
 
 // Minimum resident blocks for __launch_bounds__: the FP64-family kernels at
-// 64 threads need six (<= 170 registers); the 4-byte kernels are not capped
-// (64- and 85-register caps spill and measured slower at 24^3x8 and 48^3x12),
-// nor is FP64 reconstruct-8, whose rebuild would spill under the cap.
+// 64 threads need six (<= 170 registers); the FP16 kernels with FP16 links
+// (mixed-precision products, 120-122 registers uncapped) five blocks of 128
+// or ten of 64 (96 registers, 20 warps per SM instead of 16, to hide their
+// memory latency); the other 4-byte kernels are not capped (64- and
+// 85-register caps spill and measured slower at 24^3x8 and 48^3x12), nor is
+// FP64 reconstruct-8, whose rebuild would spill under the cap.
 template <typename SF, typename GF, int TPB>
 __host__ __device__ constexpr int dslash_min_blocks_tpb()
 {
-    return sizeof(typename SF::R) == 8 && GF::kRecon_ != 8 ? (TPB == 64 ? 6 : 1) : 1;
+    if constexpr (sizeof(typename SF::R) == 8 && GF::kRecon_ != 8) return TPB == 64 ? 6 : 1;
+    if constexpr (is_fp16_spinor<SF>::value && is_fp16_links<GF>::value) return TPB == 64 ? 10 : TPB == 128 ? 5 : 2;
+    return 1;
 }
 
 template <typename SF, typename GF, int kDagger, int kEpi, bool kReduce, int TPB,
