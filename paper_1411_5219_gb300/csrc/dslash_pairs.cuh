@@ -277,8 +277,15 @@ __device__ __forceinline__ float fmah(unsigned short a, unsigned short b, float 
     return d;
 }
 
-__device__ __forceinline__ __half2 neg_im(__half2 w) { return __hmul2(w, __floats2half2_rn(1.0f, -1.0f)); }
-__device__ __forceinline__ __half2 neg_re(__half2 w) { return __hmul2(w, __floats2half2_rn(-1.0f, 1.0f)); }
+// sign flips as integer operations (off the FMA pipe)
+__device__ __forceinline__ __half2 flip_bits(__half2 w, uint32_t m)
+{
+    const uint32_t u = *reinterpret_cast<uint32_t *>(&w) ^ m;
+    return as_h2(u);
+}
+__device__ __forceinline__ __half2 neg_im(__half2 w) { return flip_bits(w, 0x80000000u); }
+__device__ __forceinline__ __half2 neg_re(__half2 w) { return flip_bits(w, 0x00008000u); }
+__device__ __forceinline__ __half2 neg_both(__half2 w) { return flip_bits(w, 0x80008000u); }
 
 // U (kAdj false) or U^dagger (kAdj true) times the two half-spinor spins,
 // from the link's half2 words (u[row][col]), into FP32 pairs.
@@ -349,8 +356,8 @@ __device__ __forceinline__ void link_words(const typename GF::Raw &r, __half2 (&
             halves(u[1][b], br, bi);
             halves(u[0][b], cr, ci);
             halves(u[1][a], dr, di);
-            halves(__hneg2(u[0][a]), nar, nai);
-            halves(__hneg2(u[0][b]), ncr, nci);
+            halves(neg_both(u[0][a]), nar, nai);
+            halves(neg_both(u[0][b]), ncr, nci);
             // Re P = ar br - ai bi - cr dr + ci di
             float re = fmah(ar, br, 0.0f);
             re = fmah(nai, bi, re);
