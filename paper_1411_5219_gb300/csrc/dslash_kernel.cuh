@@ -262,8 +262,8 @@ __host__ __device__ constexpr int dslash_min_blocks()
 }
 
 // Minimum resident blocks for __launch_bounds__: the FP64-family kernels at
-// 64 threads need six (<= 170 registers); the FP16 kernels with FP16 links
-// (mixed-precision products, 120-122 registers uncapped) five blocks of 128
+// 64 threads need six (<= 170 registers); the 16-bit kernels with 16-bit
+// links (mixed-precision products, 120-122 registers uncapped) five blocks of 128
 // or ten of 64 (96 registers, 20 warps per SM instead of 16, to hide their
 // memory latency); the other 4-byte kernels are not capped (64- and
 // 85-register caps spill and measured slower at 24^3x8 and 48^3x12), nor is
@@ -272,7 +272,7 @@ template <typename SF, typename GF, int TPB>
 __host__ __device__ constexpr int dslash_min_blocks_tpb()
 {
     if constexpr (sizeof(typename SF::R) == 8 && GF::kRecon_ != 8) return TPB == 64 ? 6 : 1;
-    if constexpr (is_fp16_spinor<SF>::value && is_fp16_links<GF>::value) return TPB == 64 ? 10 : TPB == 128 ? 5 : 2;
+    if constexpr (is_mixed16<SF, GF>::value) return TPB == 64 ? 10 : TPB == 128 ? 5 : 2;
     return 1;
 }
 

@@ -90,33 +90,87 @@ struct is_fp16_spinor<Sp16<__half, N>> : std::true_type {};
 
 __device__ __forceinline__ __half2 as_h2(uint32_t w) { return *reinterpret_cast<__half2 *>(&w); }
 
-// FP16 spinors: the spin projection in half2 arithmetic on the stored (re,
-// im) words: hw[s][c] = h_s of colour c as a half2 word.  h is rounded to
-// FP16 once more (half an FP16 unit of |h|, within the storage tolerance).
+// Packed 16-bit arithmetic on 32-bit words holding one complex number
+// (re in the low half, im in the high half), for FP16 and BF16, and the
+// mixed-precision FMA of sm_100+ (16-bit x 16-bit product, exact in FP32,
+// added to an FP32 value).
+template <typename H>
+struct Word16;
+template <>
+struct Word16<__half> {
+    __device__ __forceinline__ static uint32_t fma2(uint32_t a, uint32_t b, uint32_t c)
+    {
+        const __half2 d = __hfma2(*reinterpret_cast<__half2 *>(&a), *reinterpret_cast<__half2 *>(&b),
+                                  *reinterpret_cast<__half2 *>(&c));
+        return *reinterpret_cast<const uint32_t *>(&d);
+    }
+    __device__ __forceinline__ static uint32_t pack(float lo, float hi)
+    {
+        const __half2 d = __floats2half2_rn(lo, hi);
+        return *reinterpret_cast<const uint32_t *>(&d);
+    }
+    __device__ __forceinline__ static float fma(unsigned short a, unsigned short b, float c)
+    {
+        float d;
+        asm("fma.rn.f32.f16 %0, %1, %2, %3;" : "=f"(d) : "h"(a), "h"(b), "f"(c));
+        return d;
+    }
+};
+template <>
+struct Word16<__nv_bfloat16> {
+    __device__ __forceinline__ static uint32_t fma2(uint32_t a, uint32_t b, uint32_t c)
+    {
+        const __nv_bfloat162 d = __hfma2(*reinterpret_cast<__nv_bfloat162 *>(&a),
+                                         *reinterpret_cast<__nv_bfloat162 *>(&b),
+                                         *reinterpret_cast<__nv_bfloat162 *>(&c));
+        return *reinterpret_cast<const uint32_t *>(&d);
+    }
+    __device__ __forceinline__ static uint32_t pack(float lo, float hi)
+    {
+        const __nv_bfloat162 d = __floats2bfloat162_rn(lo, hi);
+        return *reinterpret_cast<const uint32_t *>(&d);
+    }
+    __device__ __forceinline__ static float fma(unsigned short a, unsigned short b, float c)
+    {
+        float d;
+        asm("fma.rn.f32.bf16 %0, %1, %2, %3;" : "=f"(d) : "h"(a), "h"(b), "f"(c));
+        return d;
+    }
+};
+__device__ __forceinline__ uint32_t swap_halves(uint32_t w) { return __byte_perm(w, 0, 0x1032); }
+// sign flips as integer operations (off the FMA pipe)
+__device__ __forceinline__ uint32_t neg_im(uint32_t w) { return w ^ 0x80000000u; }
+__device__ __forceinline__ uint32_t neg_re(uint32_t w) { return w ^ 0x00008000u; }
+__device__ __forceinline__ uint32_t neg_both(uint32_t w) { return w ^ 0x80008000u; }
+
+// 16-bit spinors: the spin projection in packed 16-bit arithmetic on the
+// stored (re, im) words: hw[s][c] = h_s of colour c as such a word.  h is
+// rounded to the 16-bit format once more (half a unit of |h|, within the
+// storage tolerance).
 template <typename SF, int MU, int S>
-__device__ __forceinline__ void project_words(const typename SF::Raw &w, __half2 (&hw)[2][3])
+__device__ __forceinline__ void project_words(const typename SF::Raw &w, uint32_t (&hw)[2][3])
 {
     using H = typename SF::H16;
+    using W = Word16<H>;
     constexpr int b0 = MU <= 1 ? 3 : 2, b1 = MU <= 1 ? 2 : 3;
     constexpr float s = (float)S;
-    const __half2 pp = __floats2half2_rn(s, s), mm = __floats2half2_rn(-s, -s);
-    const __half2 mp = __floats2half2_rn(-s, s), pm = __floats2half2_rn(s, -s);
+    const uint32_t pp = W::pack(s, s), mm = W::pack(-s, -s), mp = W::pack(-s, s), pm = W::pack(s, -s);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const __half2 a0 = as_h2(word16<H>(w.w, c)), a1 = as_h2(word16<H>(w.w, 3 + c));
-        const __half2 x0 = as_h2(word16<H>(w.w, 3 * b0 + c)), x1 = as_h2(word16<H>(w.w, 3 * b1 + c));
+        const uint32_t a0 = word16<H>(w.w, c), a1 = word16<H>(w.w, 3 + c);
+        const uint32_t x0 = word16<H>(w.w, 3 * b0 + c), x1 = word16<H>(w.w, 3 * b1 + c);
         if (MU == 0) {  // (psi0 + S i psi3, psi1 + S i psi2); i z = (-im, re)
-            hw[0][c] = __hfma2(__lowhigh2highlow(x0), mp, a0);
-            hw[1][c] = __hfma2(__lowhigh2highlow(x1), mp, a1);
+            hw[0][c] = W::fma2(swap_halves(x0), mp, a0);
+            hw[1][c] = W::fma2(swap_halves(x1), mp, a1);
         } else if (MU == 1) {  // (psi0 + S psi3, psi1 - S psi2)
-            hw[0][c] = __hfma2(x0, pp, a0);
-            hw[1][c] = __hfma2(x1, mm, a1);
+            hw[0][c] = W::fma2(x0, pp, a0);
+            hw[1][c] = W::fma2(x1, mm, a1);
         } else if (MU == 2) {  // (psi0 + S i psi2, psi1 - S i psi3)
-            hw[0][c] = __hfma2(__lowhigh2highlow(x0), mp, a0);
-            hw[1][c] = __hfma2(__lowhigh2highlow(x1), pm, a1);
+            hw[0][c] = W::fma2(swap_halves(x0), mp, a0);
+            hw[1][c] = W::fma2(swap_halves(x1), pm, a1);
         } else {  // (psi0 - S psi2, psi1 - S psi3)
-            hw[0][c] = __hfma2(x0, mm, a0);
-            hw[1][c] = __hfma2(x1, mm, a1);
+            hw[0][c] = W::fma2(x0, mm, a0);
+            hw[1][c] = W::fma2(x1, mm, a1);
         }
     }
 }
@@ -130,11 +184,11 @@ __device__ __forceinline__ HalfPairs project_pairs(const typename SF::Raw &w)
     HalfPairs h;
     if constexpr (is_fp16_spinor<SF>::value) {
         // 12 conversions to FP32 instead of 24 (they run on the FMA pipe)
-        __half2 hw[2][3];
+        uint32_t hw[2][3];
         project_words<SF, MU, S>(w, hw);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const float2 f0 = __half22float2(hw[0][c]), f1 = __half22float2(hw[1][c]);
+            const float2 f0 = __half22float2(as_h2(hw[0][c])), f1 = __half22float2(as_h2(hw[1][c]));
             h.r[c] = make_float2(f0.x, f1.x);
             h.i[c] = make_float2(f0.y, f1.y);
         }
@@ -248,50 +302,33 @@ __device__ __forceinline__ void accumulate_pairs(AccPairs &acc, const HalfPairs 
     }
 }
 
-// ---- FP16 spinors with FP16 links (reconstruct 12 or 18): the SU(3)
-// product by mixed-precision FMA (fma.rn.f32.f16: an FP16 x FP16 product,
-// exact in FP32, added to an FP32 value) straight from the stored link words
-// and the half2-projected half spinor, so neither needs converting to FP32
-// and no link entry is copied into both lanes of a pair.  Measured on
-// GB300: the mixed FMA issues at the FFMA rate, and with operands taken from
-// the halves of 32-bit words it ran 25 % above conversions plus packed FMAs.
+// ---- 16-bit spinors with links of the same 16-bit format (reconstruct 12
+// or 18): the SU(3) product by mixed-precision FMA straight from the stored
+// link words and the packed-projected half spinor, so neither needs
+// converting to FP32 and no link entry is copied into both lanes of a pair.
+// Measured on GB300: fma.rn.f32.f16 issues at the FFMA rate, and with
+// operands taken from the halves of 32-bit words it ran 25 % above
+// conversions plus packed FMAs.
 
-template <typename GF>
-struct is_fp16_links : std::false_type {};
-template <>
-struct is_fp16_links<G16<__half, 12>> : std::true_type {};
-template <>
-struct is_fp16_links<G16<__half, 18>> : std::true_type {};
+template <typename SF, typename GF>
+struct is_mixed16 : std::false_type {};
+template <typename H, bool N>
+struct is_mixed16<Sp16<H, N>, G16<H, 12>> : std::true_type {};
+template <typename H, bool N>
+struct is_mixed16<Sp16<H, N>, G16<H, 18>> : std::true_type {};
 
-// the (re, im) halves of a half2 word as 16-bit registers
-__device__ __forceinline__ void halves(__half2 w, unsigned short &re, unsigned short &im)
+// the (re, im) halves of a word as 16-bit registers
+__device__ __forceinline__ void halves(uint32_t w, unsigned short &re, unsigned short &im)
 {
-    const uint32_t u = *reinterpret_cast<uint32_t *>(&w);
-    asm("mov.b32 {%0, %1}, %2;" : "=h"(re), "=h"(im) : "r"(u));
+    asm("mov.b32 {%0, %1}, %2;" : "=h"(re), "=h"(im) : "r"(w));
 }
-
-__device__ __forceinline__ float fmah(unsigned short a, unsigned short b, float c)
-{
-    float d;
-    asm("fma.rn.f32.f16 %0, %1, %2, %3;" : "=f"(d) : "h"(a), "h"(b), "f"(c));
-    return d;
-}
-
-// sign flips as integer operations (off the FMA pipe)
-__device__ __forceinline__ __half2 flip_bits(__half2 w, uint32_t m)
-{
-    const uint32_t u = *reinterpret_cast<uint32_t *>(&w) ^ m;
-    return as_h2(u);
-}
-__device__ __forceinline__ __half2 neg_im(__half2 w) { return flip_bits(w, 0x80000000u); }
-__device__ __forceinline__ __half2 neg_re(__half2 w) { return flip_bits(w, 0x00008000u); }
-__device__ __forceinline__ __half2 neg_both(__half2 w) { return flip_bits(w, 0x80008000u); }
 
 // U (kAdj false) or U^dagger (kAdj true) times the two half-spinor spins,
-// from the link's half2 words (u[row][col]), into FP32 pairs.
-template <bool kAdj>
-__device__ __forceinline__ HalfPairs su3_mixed(const __half2 (&u)[3][3], const __half2 (&hw)[2][3])
+// from the link's words (u[row][col]), into FP32 pairs.
+template <typename H, bool kAdj>
+__device__ __forceinline__ HalfPairs su3_mixed(const uint32_t (&u)[3][3], const uint32_t (&hw)[2][3])
 {
+    using W = Word16<H>;
     // re and im halves of h, and of h with one part negated (the minus signs
     // of the complex products)
     unsigned short hr[2][3], hi[2][3], hn[2][3];
@@ -318,15 +355,15 @@ __device__ __forceinline__ HalfPairs su3_mixed(const __half2 (&u)[3][3], const _
                 unsigned short ur, ui;
                 halves(kAdj ? u[b][a] : u[a][b], ur, ui);
                 if (!kAdj) {  // Re += ur hr - ui hi ; Im += ur hi + ui hr
-                    r_ = fmah(ur, hr[s][b], r_);
-                    r_ = fmah(ui, hn[s][b], r_);
-                    i_ = fmah(ur, hi[s][b], i_);
-                    i_ = fmah(ui, hr[s][b], i_);
+                    r_ = W::fma(ur, hr[s][b], r_);
+                    r_ = W::fma(ui, hn[s][b], r_);
+                    i_ = W::fma(ur, hi[s][b], i_);
+                    i_ = W::fma(ui, hr[s][b], i_);
                 } else {  // conj(U_ba) h: Re += ur hr + ui hi ; Im += ur hi - ui hr
-                    r_ = fmah(ur, hr[s][b], r_);
-                    r_ = fmah(ui, hi[s][b], r_);
-                    i_ = fmah(ur, hi[s][b], i_);
-                    i_ = fmah(ui, hn[s][b], i_);
+                    r_ = W::fma(ur, hr[s][b], r_);
+                    r_ = W::fma(ui, hi[s][b], r_);
+                    i_ = W::fma(ur, hi[s][b], i_);
+                    i_ = W::fma(ui, hn[s][b], i_);
                 }
             }
             re[s] = r_;
@@ -338,15 +375,16 @@ __device__ __forceinline__ HalfPairs su3_mixed(const __half2 (&u)[3][3], const _
     return v;
 }
 
-// The link as half2 words; reconstruct-12 rebuilds row 2 = conj(row 0 x
-// row 1) from the stored FP16 rows with exact products and FP32 sums, and
-// rounds it to FP16 (half an FP16 unit per entry).
-template <typename GF>
-__device__ __forceinline__ void link_words(const typename GF::Raw &r, __half2 (&u)[3][3])
+// The link as words; reconstruct-12 rebuilds row 2 = conj(row 0 x row 1)
+// from the stored rows with exact products and FP32 sums, and rounds it to
+// the 16-bit format (half a unit per entry).
+template <typename H, int kRecon>
+__device__ __forceinline__ void link_words(const typename G16<H, kRecon>::Raw &r, uint32_t (&u)[3][3])
 {
+    using W = Word16<H>;
 #pragma unroll
-    for (int k = 0; k < GF::kRecon_ / 2; ++k) u[k / 3][k % 3] = as_h2(r.w[k]);
-    if constexpr (GF::kRecon_ == 12) {
+    for (int k = 0; k < kRecon / 2; ++k) u[k / 3][k % 3] = r.w[k];
+    if constexpr (kRecon == 12) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const int a = (c + 1) % 3, b = (c + 2) % 3;
@@ -359,16 +397,16 @@ __device__ __forceinline__ void link_words(const typename GF::Raw &r, __half2 (&
             halves(neg_both(u[0][a]), nar, nai);
             halves(neg_both(u[0][b]), ncr, nci);
             // Re P = ar br - ai bi - cr dr + ci di
-            float re = fmah(ar, br, 0.0f);
-            re = fmah(nai, bi, re);
-            re = fmah(ncr, dr, re);
-            re = fmah(ci, di, re);
+            float re = W::fma(ar, br, 0.0f);
+            re = W::fma(nai, bi, re);
+            re = W::fma(ncr, dr, re);
+            re = W::fma(ci, di, re);
             // -Im P = -(ar bi + ai br) + cr di + ci dr
-            float mi = fmah(nar, bi, 0.0f);
-            mi = fmah(nai, br, mi);
-            mi = fmah(cr, di, mi);
-            mi = fmah(ci, dr, mi);
-            u[2][c] = __floats2half2_rn(re, mi);
+            float mi = W::fma(nar, bi, 0.0f);
+            mi = W::fma(nai, br, mi);
+            mi = W::fma(cr, di, mi);
+            mi = W::fma(ci, dr, mi);
+            u[2][c] = W::pack(re, mi);
         }
     }
 }
@@ -381,11 +419,12 @@ __device__ __forceinline__ void hop_pairs(AccPairs &acc, const typename SF::Raw 
                                           bool flip)
 {
     HalfPairs v;
-    if constexpr (is_fp16_spinor<SF>::value && is_fp16_links<GF>::value) {
-        __half2 hw[2][3], u[3][3];
+    if constexpr (is_mixed16<SF, GF>::value) {
+        using H = typename SF::H16;
+        uint32_t hw[2][3], u[3][3];
         project_words<SF, MU, S>(rs, hw);
-        link_words<GF>(ru, u);
-        v = su3_mixed<kAdj>(u, hw);
+        link_words<H, GF::kRecon_>(ru, u);
+        v = su3_mixed<H, kAdj>(u, hw);
     } else {
         const HalfPairs h = project_pairs<SF, MU, S>(rs);
         v = su3_pairs<kAdj>(GF::decode(ru), h);
