@@ -241,9 +241,29 @@ def hot_per_launch(torch, fn, k):
 
 # ------------------------------------------------------------------ extras
 
+def back_to_back_cold(torch, fns, n=60):
+    """Seconds per launch of n back-to-back launches that cycle through
+    len(fns) independent field sets, each larger than L2: every launch reads
+    a set that the launches since its last use have evicted, and no L2 flush
+    or per-launch event record sits between the timed kernels."""
+    s = torch.cuda.current_stream()
+    for fn in fns:
+        fn()
+    torch.cuda._sleep(2_000_000)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for j in range(n):
+        fns[j % len(fns)]()
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) * 1e-3 / n
+
+
 def dslash_sweep(qcd, torch, flush, hbm, reps=20, fields=None):
     """Cold-L2 (flushed) and hot-L2 D_eo timings per volume and format; the
-    host gauge fields are kept in `fields` for the CPU oracle timings."""
+    host gauge fields are kept in `fields` for the CPU oracle timings.  At
+    48^3x12, where one format's gauge field and two half spinors exceed L2,
+    also back-to-back cold launches over three such sets."""
     from paper_1411_5219_gb300 import synthetic as syn
     out = {}
     fmts = [("f64", 18, 1536), ("f64", 12, 1152), ("f32", 12, 576), ("f16", 12, 296), ("bf16", 12, 288),
@@ -256,9 +276,13 @@ def dslash_sweep(qcd, torch, flush, hbm, reps=20, fields=None):
             fields[dims] = (U, syn.to_half(psi, 1))
         h = lat.volume // 2
         row = {}
+        b2b = dims == (48, 48, 48, 12)
         for recon in (18, 12, 8):
-            g = qcd.Gauge(lat, "f64", recon)
-            g.upload(U)
+            gs = []
+            for _ in range(3 if b2b else 1):
+                gs.append(qcd.Gauge(lat, "f64", recon))
+                gs[-1].upload(U)
+            g = gs[0]
             for prec, rc, bps in fmts:
                 if rc != recon:
                     continue
@@ -271,11 +295,22 @@ def dslash_sweep(qcd, torch, flush, hbm, reps=20, fields=None):
                 t = float(np.median(ts))
                 t_hot = hot_per_launch(torch, fn, reps)
                 gbs = h * bps / t / 1e9
-                row[f"{prec}_r{recon}"] = {"us": round(t * 1e6, 2), "GB_s": round(gbs, 1),
-                                           "frac_hbm": round(gbs / hbm, 3),
-                                           "TFLOP_s": round(h * 1320 / t / 1e12, 3),
-                                           "hot_us": round(t_hot * 1e6, 2)}
-            del g
+                ent = {"us": round(t * 1e6, 2), "GB_s": round(gbs, 1), "frac_hbm": round(gbs / hbm, 3),
+                       "TFLOP_s": round(h * 1320 / t / 1e12, 3), "hot_us": round(t_hot * 1e6, 2)}
+                if b2b:
+                    sets = [(gs[0], si, so)]
+                    for gk in gs[1:]:
+                        sik, sok = qcd.Spinor(lat, "odd", prec), qcd.Spinor(lat, "even", prec)
+                        sik.upload(syn.to_half(psi, 1))
+                        sets.append((gk, sik, sok))
+                    fns = [(lambda gk=gk, ok=ok, ik=ik: qcd.apply_dslash(gk, ok, ik)) for gk, ik, ok in sets]
+                    tb = back_to_back_cold(torch, fns)
+                    ent["b2b_us"] = round(tb * 1e6, 2)
+                    ent["b2b_frac_hbm"] = round(h * bps / tb / 1e9 / hbm, 3)
+                    ent["b2b_TFLOP_s"] = round(h * 1320 / tb / 1e12, 3)
+                    del sets, fns
+                row[f"{prec}_r{recon}"] = ent
+            del g, gs
         out["x".join(map(str, dims))] = row
         del lat
     return out
@@ -852,8 +887,10 @@ def main():
         line["dslash_ks_sweep"] = dslash_ks_sweep(qcd, torch, flush, hbm)
         host_fields = {}
         line["dslash_sweep"] = dslash_sweep(qcd, torch, flush, hbm, fields=host_fields)
-        line["dslash_sweep_note"] = (f"us: cold L2 (flushed before each launch), hot_us: mean of back-to-back "
-                                     f"launches queued behind a spin kernel (warm L2); GB/s on "
+        line["dslash_sweep_note"] = (f"us: cold L2 (flushed before each launch, one event-timed launch), hot_us: "
+                                     f"mean of back-to-back launches queued behind a spin kernel (warm L2); b2b_us "
+                                     f"(48^3x12): mean of 60 back-to-back launches cycling through three field sets "
+                                     f"of more than L2 each (cold, no per-launch flush or event); GB/s on "
                                      f"compulsory bytes per output site (cold); frac of {hbm_kind} HBM {hbm} GB/s")
         try:
             cb = cpu_oracle_sample()
@@ -874,8 +911,11 @@ def main():
         line["batched_multi_rhs_detail"] = batched
         line["serving_detail"] = serving
         line["many_systems_detail"] = many
-        line["dslash_48x48x48x12_frac_hbm"] = {k: v["frac_hbm"] for k, v in line["dslash_sweep"]["48x48x48x12"].items()
+        row48 = line["dslash_sweep"]["48x48x48x12"]
+        line["dslash_48x48x48x12_frac_hbm"] = {k: v["frac_hbm"] for k, v in row48.items()
                                                if k in ("f32_r12", "f16_r12", "bf16_r12")}
+        line["dslash_48x48x48x12_frac_hbm"]["back_to_back_cold"] = {
+            k: v.get("b2b_frac_hbm") for k, v in row48.items() if k in ("f32_r12", "f16_r12", "bf16_r12")}
         line["many_systems"] = {k: _sig(many[k], 3) for k in ("many_solves_s", "speedup_vs_fp64", "speedup_vs_mixed")}
         line["batched_multi_rhs"] = batched_summary(batched)
         line["serving"] = serving_summary(serving)
